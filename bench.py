@@ -1,0 +1,339 @@
+#!/usr/bin/env python3
+"""Throughput of the spectral Poisson solve -Δu = f (periodic, unit cube).
+
+One step = one full solve (forward 3D FFT, division by 4π²|k|², inverse 3D
+FFT) of the 512^3 FP32 sharp-source workload: one periodised Gaussian of
+width 0.01 plus 4 smooth modes (|k| <= 4), mean removed, seeded.  Inputs and
+outputs (512 MiB each) are larger than L2, so no flush is needed between
+steps.  Prints one JSON line on rank 0.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Multi-GPU: one process per GPU under torchrun; the solve does not shard, so
+every rank runs an independent replica (weak scaling, no collective on the
+data path); value = units of all ranks / max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("unknowns/s & % HBM roofline at 512³; TC/batched vs plain FP32 at rel-L2 ≤1e-5")
+UNIT = "unknowns/s"
+WORKLOAD = "sharp_source 512^3: 1 periodised Gaussian sigma=0.01 + 4 modes |k|<=4, mean removed"
+BYTES_PER_UNKNOWN_PER_PASS = 8  # FP32: each pass reads and writes the whole array once
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--grid", type=int, default=512)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# ----------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str | None):
+        self.proc = None
+        self.gpu_id = gpu_id
+
+    def start(self):
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "100"]
+        if self.gpu_id:
+            cmd += ["-i", self.gpu_id]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def gpu_uuid(torch, dev):
+    try:
+        u = str(torch.cuda.get_device_properties(dev).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        return None
+
+
+def kernel_digest() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1408_6497_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(f.encode())
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel: str, grid: int):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it
+    was taken on the current kernel sources; else None."""
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as fh:
+        d = json.load(fh)
+    if d.get("kernel_digest") != kernel_digest():
+        return None
+    e = d.get("kernels", {}).get(kernel)
+    if not e:
+        return None
+    scale = (grid ** 3) / float(e.get("unknowns", grid ** 3))
+    return float(e["dram_bytes_per_launch"]) * scale
+
+
+# --------------------------------------------------------------- oracle
+def oracle_rate(grid: int, max_seconds: float, min_reps: int = 1):
+    """Unknowns/s of the FP64 CPU oracle (as it stands) on the same source
+    sampled on a grid^3 mesh; repeats until max_seconds is used."""
+    import oracle
+    from paper_1408_6497_gb300 import workloads as wl
+    oracle.build()
+    f = wl.sharp_source((grid,) * 3).f
+    times = []
+    t_all = time.perf_counter()
+    while len(times) < min_reps or (time.perf_counter() - t_all) < max_seconds * 0.5:
+        t0 = time.perf_counter()
+        oracle.solve(f)
+        times.append(time.perf_counter() - t0)
+        if time.perf_counter() - t_all > max_seconds:
+            break
+    t = statistics.median(times)
+    return grid ** 3 / t, t, len(times), oracle.threads()
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_1408_6497_gb300 import workloads as wl
+    oracle.build()
+    # Size each step so that warmup + steps fit in about two minutes.
+    probe_t = None
+    grid = 64
+    for g in (64, 128, 256, 512):
+        f = wl.sharp_source((g,) * 3).f
+        t0 = time.perf_counter()
+        oracle.solve(f)
+        dt = time.perf_counter() - t0
+        if (args.steps + args.warmup) * dt > 120.0 and g > 64:
+            break
+        grid, probe_t = g, dt
+        if g >= args.grid:
+            break
+    f = wl.sharp_source((grid,) * 3).f
+    for _ in range(args.warmup):
+        oracle.solve(f)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.solve(f)
+    el = time.perf_counter() - t0
+    ms = el / args.steps * 1e3
+    value = grid ** 3 / (el / args.steps)
+    sample = (f"{args.steps} FP64 oracle solves of the same source on a {grid}^3 grid "
+              f"(each step bounded so the run ends within minutes)")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD.replace("512^3", f"{grid}^3 sample of the 512^3 workload"),
+                       "grid": [grid] * 3, "precision": "f64", "device": "host cores"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ ours
+def run_ours(args):
+    import torch
+    ws, rank, local = dist_env()
+    if not torch.cuda.is_available():
+        print(json.dumps({"impl": "ours", "error": "no CUDA device"}))
+        return 1
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_1408_6497_gb300 import Plan, build
+    from paper_1408_6497_gb300 import workloads as wl
+    build.build()
+
+    n = args.grid
+    shape = (n, n, n)
+    N = n ** 3
+    f_host = torch.from_numpy(wl.sharp_source(shape).f.astype(np.float32).ravel())
+    f_pin = f_host.pin_memory()
+    u_pin = torch.empty_like(f_pin).pin_memory()
+    f = f_pin.to(dev)
+    u = torch.empty_like(f)
+    plan = Plan(shape, dtype="f32", device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    for _ in range(max(3, args.warmup)):
+        plan.execute(f, u)
+    torch.cuda.synchronize(dev)
+
+    sampler = ClockSampler(gpu_uuid(torch, dev))
+    sampler.start()
+    soak_end = time.perf_counter() + 2.0
+    while time.perf_counter() < soak_end:  # bring clocks to steady state under load
+        for _ in range(20):
+            plan.execute(f, u)
+        torch.cuda.synchronize(dev)
+
+    plan.set_profiling(True)
+    barrier()
+    torch.cuda.synchronize(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        plan.execute(f, u)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier()
+    clocks = sampler.stop()
+    el_ms = e0.elapsed_time(e1)
+    plan.set_profiling(False)
+    pass_ms, nsol = plan.pass_times()
+
+    # End to end through the public host-buffer entry point.
+    e2e_steps = max(3, min(args.steps, 10))
+    plan.execute_host(f_pin, u_pin)  # allocates the plan's staging buffer
+    barrier()
+    torch.cuda.synchronize(dev)
+    h0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        plan.execute_host(f_pin, u_pin)
+    e2e_s = (time.perf_counter() - h0) / e2e_steps
+    barrier()
+
+    if dist is not None:
+        t = torch.tensor([el_ms, e2e_s], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        el_ms, e2e_s = float(t[0]), float(t[1])
+
+    ms_per_step = el_ms / args.steps
+    value = ws * N / (ms_per_step * 1e-3)
+    avg = {k: v / max(1, nsol) for k, v in pass_ms.items()}
+    top = max(avg, key=avg.get)
+    peak, peak_kind = peaks()
+    algo_bytes = BYTES_PER_UNKNOWN_PER_PASS * N
+    achieved = algo_bytes / (avg[top] * 1e-3) / 1e9
+    kernel_name = {"zfwd": "k_zfwd", "yfwd": "k_ypass", "xdiv": "k_xfused", "yinv": "k_ypass",
+                   "zinv": "k_zinv"}[top]
+    traffic = recorded_traffic(kernel_name, n)
+
+    if rank != 0:
+        return 0
+    line = {
+        "impl": "ours", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "grid": list(shape), "precision": "f32",
+                   "l2": "inputs larger than L2 (512 MiB f and u), no flush",
+                   "parallelism": "replicas" if ws > 1 else "single GPU",
+                   "clock_window": "2 s soak + timed region"},
+        "roofline": {"bound": "hbm", "kernel": top, "achieved": achieved, "peak": peak,
+                     "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": traffic,
+                     "algorithmic_bytes_per_launch": algo_bytes},
+        "passes_ms": {k: round(v, 5) for k, v in avg.items()},
+        "min_traffic_frac": (8 * N / (ms_per_step * 1e-3) / 1e9) / peak,
+        "e2e": {"value": ws * N / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 4 * N,
+                "d2h_bytes_per_step": 4 * N},
+        "gpu_launches": plan.launches_per_solve * args.steps,
+        "clocks": clocks,
+    }
+    if ws == 1 and not args.no_cpu_baseline:
+        rate, t, reps, cores = oracle_rate(min(n, 256), max_seconds=20.0)
+        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                "sample": f"{reps} FP64 oracle solve(s) of the same source on a "
+                                          f"{min(n, 256)}^3 grid, median {t:.2f} s"}
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

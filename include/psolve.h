@@ -1,0 +1,147 @@
+/*
+ * psolve — spectral Poisson solver for -Δu = f, periodic on the unit cube,
+ * as hand-written CUDA kernels for one GB300 (sm_103a).  C ABI.
+ *
+ * The operation (§1, Eq. 1.1; §2.1; §3 of Gholami, Malhotra, Sundar, Biros,
+ * "FFT, FMM, or Multigrid?"): forward 3D FFT of f, Hadamard product with the
+ * inverse of the Laplacian's diagonal (spectral) form, inverse 3D FFT:
+ *
+ *     u = A f,   A = F^{-1} D F,   D(k) = 1 / (4π² |k|²),   D(0) = 0,
+ *
+ * on the grid x_j = j/n_i (j = 0..n_i-1) per axis, with signed wavenumbers
+ * k(j) = j for j <= n/2, j - n otherwise (the Nyquist index counts as +n/2;
+ * only k² enters D).  The mean of f is projected out (û(0) = 0), so u has
+ * zero mean and the caller need not subtract the mean of f.
+ *
+ * Arrays.  f and u are real, C-order (nx, ny, nz) with z contiguous, in the
+ * plan's precision (double for PSOLVE_F64, float otherwise).  A plan with
+ * batch B > 1 takes B instances back to back: instance b starts at element
+ * psolve_instance_offset(plan, b).  Pointers passed to psolve_execute and
+ * psolve_adjoint are DEVICE pointers on the plan's device, 16-byte aligned.
+ *
+ * Streams.  Every `stream` argument is a cudaStream_t passed as void*
+ * (NULL = the legacy default stream).  Execution is asynchronous on that
+ * stream; the library never synchronises it except where stated.
+ *
+ * Errors.  Every call returns a psolve_status.  Host-detectable problems
+ * (bad sizes, null or misaligned pointers, partial aliasing, a destroyed
+ * plan) are returned before anything is enqueued.  A CUDA launch or copy
+ * failure returns PSOLVE_ERR_CUDA.  Asynchronous device-side errors are
+ * recorded in the plan's device status word and read by psolve_get_status.
+ * psolve_last_error() gives a human-readable message for the calling thread.
+ */
+#ifndef PSOLVE_H
+#define PSOLVE_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PSOLVE_F64 = 0,     /* double in, double out, FP64 butterflies          */
+    PSOLVE_F32 = 1,     /* float in, float out, FP32 butterflies            */
+    PSOLVE_F32_TC = 2   /* float in/out; radix-16 stages on tensor cores     */
+} psolve_dtype;
+
+typedef enum {
+    PSOLVE_OK = 0,
+    PSOLVE_ERR_INVALID_ARG = 1,      /* null/misaligned pointer, bad batch, bad dtype, partial overlap */
+    PSOLVE_ERR_UNSUPPORTED_SIZE = 2, /* an n is not 2^a 3^b, is odd, < 4 or > 2048                    */
+    PSOLVE_ERR_OOM = 3,              /* device allocation failed                                       */
+    PSOLVE_ERR_CUDA = 4,             /* a CUDA call failed (no device, launch error, ...)              */
+    PSOLVE_ERR_TIMEOUT = 5,          /* a bounded device-side wait gave up                             */
+    PSOLVE_ERR_INTERNAL = 6          /* a device-side consistency check failed                         */
+} psolve_status;
+
+typedef struct psolve_plan psolve_plan;
+
+/* Create a plan for `batch` equal grids nx × ny × nz (§3: the setup is paid
+ * once and amortised over solves with new right-hand sides).  Each n must
+ * be 2^a·3^b, even, 4 <= n <= 2048.  Allocates the plan's twiddle tables
+ * (computed on the device in FP64) and status word on the current device.
+ * The spectrum is formed inside u itself, so no workspace of the grid's
+ * size is allocated.  On success *out owns the plan; release it with
+ * psolve_destroy.  On failure *out is set to NULL. */
+psolve_status psolve_plan_create(int nx, int ny, int nz, int dtype, int batch,
+                                 psolve_plan **out);
+
+/* Create a plan for `batch` grids of unequal sizes (nx[b], ny[b], nz[b]),
+ * solved together.  Instance b starts at element psolve_instance_offset(b)
+ * of the packed f/u arrays; offsets are aligned up to 32 elements. */
+psolve_status psolve_plan_create_many(const int *nx, const int *ny, const int *nz, int batch,
+                                      int dtype, psolve_plan **out);
+
+/* u = A f for every instance (§2.1).  f, u: device pointers holding
+ * psolve_total_elements(plan) values.  u == f (in place) is allowed; any
+ * other overlap is PSOLVE_ERR_INVALID_ARG.  f is not modified unless u == f. */
+psolve_status psolve_execute(psolve_plan *plan, const void *f, void *u, void *stream);
+
+/* grad_f = A^T g.  A is real symmetric (D is real and even in k), so this is
+ * the same operator; it is the backward of psolve_execute. */
+psolve_status psolve_adjoint(psolve_plan *plan, const void *g, void *grad_f, void *stream);
+
+/* psolve_execute on HOST buffers: copies f_host to the device, solves, copies
+ * u back, all on `stream`, and synchronises the stream before returning.
+ * Uses a device buffer owned by the plan (allocated on first use). */
+psolve_status psolve_execute_host(psolve_plan *plan, const void *f_host, void *u_host,
+                                  void *stream);
+
+/* Free everything the plan owns.  The plan pointer is invalid afterwards. */
+psolve_status psolve_destroy(psolve_plan *plan);
+
+/* Element offset of instance b in the packed f/u arrays; (size_t)-1 on error. */
+size_t psolve_instance_offset(const psolve_plan *plan, int b);
+
+/* Number of elements the packed f/u arrays hold; 0 on error. */
+size_t psolve_total_elements(const psolve_plan *plan);
+
+/* Synchronise `stream`, read and clear the plan's device status word. */
+psolve_status psolve_get_status(psolve_plan *plan, void *stream);
+
+/* Write the signed wavenumbers the division kernel uses for instance b, as
+ * computed on the device: for every spectrum index (jx, jy, jz),
+ * 0 <= jz <= nz/2, three int32 (kx, ky, kz) at
+ * kxyz_out[3 * ((jx * ny + jy) * (nz/2 + 1) + jz)].  kxyz_out is a HOST
+ * buffer of 3·nx·ny·(nz/2+1) ints.  Synchronous. */
+psolve_status psolve_debug_kvec(const psolve_plan *plan, int b, int *kxyz_out);
+
+/* FP64 reductions over n elements of two device arrays a, ref of `dtype`:
+ * out4[0] = Σ (a - ref)², out4[1] = Σ ref², out4[2] = max |a - ref|,
+ * out4[3] = max |ref|.  out4 is a HOST array of 4 doubles.  Synchronous on
+ * `stream`. */
+psolve_status psolve_error_norms(const void *a, const void *ref, size_t n, int dtype,
+                                 double *out4, void *stream);
+
+/* Per-pass timing with CUDA events recorded on the solve's own stream.
+ * After psolve_set_profiling(plan, 1), every psolve_execute/psolve_adjoint
+ * records an event before the first pass and after each pass; the kernels
+ * and their order are unchanged.  psolve_pass_times synchronises those
+ * events, writes into ms[i] the summed milliseconds of pass i over all
+ * recorded solves (at most cap passes), sets *n_passes and *n_solves, and
+ * clears the record.  psolve_set_profiling(plan, 0) stops recording. */
+psolve_status psolve_set_profiling(psolve_plan *plan, int enable);
+psolve_status psolve_pass_times(psolve_plan *plan, double *ms, int cap, int *n_passes, int *n_solves);
+
+/* Name of pass i of the plan's solve ("zfwd", "yfwd", "xdiv", "yinv",
+ * "zinv"), or NULL. */
+const char *psolve_pass_name(const psolve_plan *plan, int i);
+
+/* Number of kernel launches one psolve_execute enqueues; 0 on error. */
+int psolve_launches_per_solve(const psolve_plan *plan);
+
+/* Static description of a status code. */
+const char *psolve_status_string(psolve_status s);
+
+/* Message for the last error reported on the calling thread ("" if none). */
+const char *psolve_last_error(void);
+
+/* Library version, major*10000 + minor*100 + patch. */
+int psolve_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PSOLVE_H */

@@ -1,0 +1,635 @@
+// C-ABI of the solver: plan creation (size checks, 1D stage plans, tile
+// shapes, FP64 twiddle generation on the device) and the five-pass solve.
+// See include/psolve.h for the contract of every entry point.
+#include "psolve.h"
+#include "launch.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <vector>
+
+using namespace psolve;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+psolve_status fail(psolve_status s, const std::string &msg)
+{
+    g_last_error = msg;
+    return s;
+}
+
+psolve_status cuda_fail(cudaError_t e, const char *where)
+{
+    return fail(PSOLVE_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+constexpr unsigned kMagic = 0x50534F4Cu; // "PSOL"
+constexpr size_t kSmemCap = 200 * 1024;
+
+// Instances of equal dimensions laid out back to back at `stride` elements.
+struct Group {
+    int nx, ny, nz, M;
+    int count;
+    size_t off0, stride;
+    LinePlan pz, py, px;
+    size_t tw_z, tw_y, tw_x, post; // complex-element offsets into the table buffer
+    int Wz, Wy, Wx;
+};
+
+bool factor23(int n, int &a, int &b)
+{
+    a = b = 0;
+    if (n <= 0) return false;
+    while (n % 2 == 0) { n /= 2; ++a; }
+    while (n % 3 == 0) { n /= 3; ++b; }
+    return n == 1;
+}
+
+bool size_ok(int n)
+{
+    int a, b;
+    return n >= 4 && n <= 2048 && (n % 2) == 0 && factor23(n, a, b);
+}
+
+// Stage plan of an L-point line: radix-3 stages for the factors of 3, then
+// the largest power-of-two radices (<= 16) that divide E.
+bool make_line_plan(int L, LinePlan &p)
+{
+    int a, b;
+    if (!factor23(L, a, b) || L < 2) return false;
+    const int E = b > 0 ? 3 * (1 << std::min(a, 3)) : (1 << std::min(a, 4));
+    if (!supported_E(E)) return false;
+    std::memset(&p, 0, sizeof(p));
+    p.L = L;
+    p.E = E;
+    p.TL = L / E;
+    int p2 = 1;
+    while (E % (p2 * 2) == 0 && p2 * 2 <= 16) p2 *= 2;
+    std::vector<int> rad(b, 3);
+    int rem = 1 << a;
+    while (rem > 1) {
+        const int r = std::min(p2, rem);
+        rad.push_back(r);
+        rem /= r;
+    }
+    if ((int)rad.size() > kMaxStages) return false;
+    p.nst = (int)rad.size();
+    int ns = 1;
+    for (int s = 0; s < p.nst; ++s) {
+        p.radix[s] = rad[s];
+        p.ns[s] = ns;
+        p.twstep[s] = L / (ns * rad[s]);
+        ns *= rad[s];
+    }
+    return true;
+}
+
+size_t csize(int dtype) { return dtype == PSOLVE_F64 ? 16 : 8; }
+size_t rsize(int dtype) { return dtype == PSOLVE_F64 ? 8 : 4; }
+
+int zpitch(int M) { return M + (M >> 4) + 1; }
+size_t z_smem(const Group &g, int dtype) { return (size_t)(g.M + (size_t)g.Wz * zpitch(g.M)) * csize(dtype); }
+size_t s_smem(int L, int W, int dtype) { return (size_t)L * (1 + W) * csize(dtype); }
+
+void choose_tiles(Group &g, int dtype)
+{
+    const bool fp64 = dtype == PSOLVE_F64;
+    // z: about 256 threads, W rows each of TL threads.
+    {
+        const int mt = max_threads(fp64, g.pz.E);
+        g.Wz = std::max(1, std::min(256, mt) / g.pz.TL);
+        while (g.Wz > 1 && z_smem(g, dtype) > kSmemCap) g.Wz /= 2;
+    }
+    // y and x: W adjacent columns (16 columns = 128 B runs in FP32).
+    {
+        const int mt = max_threads(fp64, g.py.E);
+        int W = std::min(16, std::max(1, mt / g.py.TL));
+        W = std::min(W, g.M);
+        while (W > 1 && s_smem(g.ny, W, dtype) > kSmemCap) W /= 2;
+        g.Wy = std::max(1, W);
+    }
+    {
+        const int mt = max_threads(fp64, g.px.E);
+        int W = std::min(16, std::max(2, mt / g.px.TL));
+        W = std::max(2, std::min(W, std::max(2, g.M)));
+        while (W > 2 && s_smem(g.nx, W, dtype) > kSmemCap) W /= 2;
+        g.Wx = W;
+    }
+}
+
+} // namespace
+
+struct psolve_plan {
+    unsigned magic;
+    int dtype;
+    int device;
+    int batch;
+    std::vector<Group> groups;
+    std::vector<size_t> inst_off;
+    size_t total;
+    void *tables;
+    int *status;
+    void *stage;
+    size_t stage_bytes;
+    // per-pass profiling: one set of kPasses+1 events per recorded solve
+    bool profiling;
+    std::vector<std::vector<cudaEvent_t>> ev_used;
+    std::vector<std::vector<cudaEvent_t>> ev_free;
+};
+
+namespace {
+
+bool plan_ok(const psolve_plan *p) { return p != nullptr && p->magic == kMagic; }
+
+struct DeviceGuard {
+    int prev = -1;
+    bool changed = false;
+    cudaError_t err = cudaSuccess;
+    explicit DeviceGuard(int dev)
+    {
+        err = cudaGetDevice(&prev);
+        if (err == cudaSuccess && prev != dev) {
+            err = cudaSetDevice(dev);
+            changed = err == cudaSuccess;
+        }
+    }
+    ~DeviceGuard()
+    {
+        if (changed) cudaSetDevice(prev);
+    }
+};
+
+constexpr int kPasses = 5;
+const char *kPassNames[kPasses] = {"zfwd", "yfwd", "xdiv", "yinv", "zinv"};
+
+void destroy_events(psolve_plan *p)
+{
+    for (auto *pool : {&p->ev_used, &p->ev_free})
+        for (auto &set : *pool)
+            for (auto e : set) cudaEventDestroy(e);
+    p->ev_used.clear();
+    p->ev_free.clear();
+}
+
+// Events for one solve, or an empty set when profiling is off.
+std::vector<cudaEvent_t> *take_events(psolve_plan *p)
+{
+    if (!p->profiling) return nullptr;
+    std::vector<cudaEvent_t> set;
+    if (!p->ev_free.empty()) {
+        set = std::move(p->ev_free.back());
+        p->ev_free.pop_back();
+    } else {
+        set.resize(kPasses + 1);
+        for (auto &e : set)
+            if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    }
+    p->ev_used.push_back(std::move(set));
+    return &p->ev_used.back();
+}
+
+void release(psolve_plan *p)
+{
+    if (!p) return;
+    destroy_events(p);
+    if (p->tables) cudaFree(p->tables);
+    if (p->status) cudaFree(p->status);
+    if (p->stage) cudaFree(p->stage);
+    p->magic = 0;
+    delete p;
+}
+
+psolve_status build_plan(const std::vector<int> &nx, const std::vector<int> &ny, const std::vector<int> &nz,
+                         int dtype, bool uniform, psolve_plan **out)
+{
+    const int batch = (int)nx.size();
+    const size_t align = 32;
+    std::unique_ptr<psolve_plan> p(new psolve_plan());
+    p->magic = kMagic;
+    p->dtype = dtype;
+    p->batch = batch;
+    p->tables = nullptr;
+    p->status = nullptr;
+    p->stage = nullptr;
+    p->stage_bytes = 0;
+    p->profiling = false;
+    size_t off = 0;
+    for (int b = 0; b < batch; ++b) {
+        const size_t N = (size_t)nx[b] * ny[b] * nz[b];
+        if (uniform) {
+            if (b == 0) {
+                Group g{};
+                g.nx = nx[0]; g.ny = ny[0]; g.nz = nz[0]; g.M = nz[0] / 2;
+                g.count = batch; g.off0 = 0; g.stride = N;
+                p->groups.push_back(g);
+            }
+            p->inst_off.push_back((size_t)b * N);
+            off = (size_t)(b + 1) * N;
+        } else {
+            Group g{};
+            g.nx = nx[b]; g.ny = ny[b]; g.nz = nz[b]; g.M = nz[b] / 2;
+            g.count = 1; g.off0 = off; g.stride = N;
+            p->groups.push_back(g);
+            p->inst_off.push_back(off);
+            off += (N + align - 1) / align * align;
+        }
+    }
+    p->total = uniform ? off : (p->inst_off.back() + (size_t)nx.back() * ny.back() * nz.back());
+
+    // Stage plans, tile shapes and the table layout.
+    std::map<int, size_t> roots_at; // L -> offset
+    std::map<int, size_t> post_at;  // nz -> offset
+    size_t tcount = 0;
+    for (auto &g : p->groups) {
+        if (!make_line_plan(g.M, g.pz) || !make_line_plan(g.ny, g.py) || !make_line_plan(g.nx, g.px))
+            return fail(PSOLVE_ERR_UNSUPPORTED_SIZE, "no stage plan for this size");
+        choose_tiles(g, dtype);
+        for (int L : {g.M, g.ny, g.nx})
+            if (!roots_at.count(L)) { roots_at[L] = tcount; tcount += L; }
+        if (!post_at.count(g.nz)) { post_at[g.nz] = tcount; tcount += g.M; }
+        g.tw_z = roots_at[g.M];
+        g.tw_y = roots_at[g.ny];
+        g.tw_x = roots_at[g.nx];
+        g.post = post_at[g.nz];
+    }
+
+    cudaError_t e = cudaGetDevice(&p->device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    e = cudaMalloc(&p->tables, tcount * csize(dtype));
+    if (e != cudaSuccess) {
+        p->tables = nullptr;
+        release(p.release());
+        return fail(PSOLVE_ERR_OOM, "twiddle tables: cudaMalloc failed");
+    }
+    e = cudaMalloc((void **)&p->status, sizeof(int));
+    if (e != cudaSuccess) {
+        p->status = nullptr;
+        release(p.release());
+        return fail(PSOLVE_ERR_OOM, "status word: cudaMalloc failed");
+    }
+    cudaMemset(p->status, 0, sizeof(int));
+    char *tb = (char *)p->tables;
+    const size_t cs = csize(dtype);
+    for (auto &kv : roots_at) {
+        e = dtype == PSOLVE_F64 ? launch_roots<double>(tb + kv.second * cs, kv.first, kv.first, 0)
+                                : launch_roots<float>(tb + kv.second * cs, kv.first, kv.first, 0);
+        if (e != cudaSuccess) { release(p.release()); return cuda_fail(e, "twiddle generation"); }
+    }
+    for (auto &kv : post_at) {
+        e = dtype == PSOLVE_F64 ? launch_roots<double>(tb + kv.second * cs, kv.first / 2, kv.first, 0)
+                                : launch_roots<float>(tb + kv.second * cs, kv.first / 2, kv.first, 0);
+        if (e != cudaSuccess) { release(p.release()); return cuda_fail(e, "twiddle generation"); }
+    }
+    e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) { release(p.release()); return cuda_fail(e, "plan set-up"); }
+    *out = p.release();
+    return PSOLVE_OK;
+}
+
+unsigned ceil_div(long long a, long long b) { return (unsigned)((a + b - 1) / b); }
+
+template <typename T>
+psolve_status run_group(const psolve_plan *p, const Group &g, const T *f, T *u, cudaStream_t s,
+                        const std::vector<cudaEvent_t> *ev)
+{
+    auto mark = [&](int i) {
+        if (ev) cudaEventRecord((*ev)[i], s);
+    };
+    using C = typename cplx_of<T>::type;
+    const C *tab = reinterpret_cast<const C *>(p->tables);
+    const T *fi = f + g.off0;
+    T *ui = u + g.off0;
+    const int dtype = p->dtype;
+    cudaError_t e;
+
+    ZArgs<T> z{};
+    z.in = fi;
+    z.out = ui;
+    z.rows = (long long)g.count * g.nx * g.ny;
+    z.nz = g.nz;
+    z.M = g.M;
+    z.W = g.Wz;
+    z.pl = g.pz;
+    z.tw = tab + g.tw_z;
+    z.post = tab + g.post;
+    const unsigned zgrid = ceil_div(z.rows, g.Wz);
+    const unsigned zblock = (unsigned)(g.Wz * g.pz.TL);
+    mark(0);
+    e = launch_zfwd<T>(z, zgrid, zblock, z_smem(g, dtype), s);
+    if (e != cudaSuccess) return cuda_fail(e, "z forward pass");
+    mark(1);
+
+    SArgs<T> y{};
+    y.data = ui;
+    y.nplanes = (long long)g.count * g.nx;
+    y.sPlane = (long long)g.ny * g.M;
+    y.sL = g.M;
+    y.M = g.M;
+    y.W = g.Wy;
+    y.ncb = (g.M + g.Wy - 1) / g.Wy;
+    y.pl = g.py;
+    y.tw = tab + g.tw_y;
+    const unsigned ygrid = (unsigned)(y.nplanes * y.ncb);
+    const unsigned yblock = (unsigned)(g.Wy * g.py.TL);
+    const size_t ysm = s_smem(g.ny, g.Wy, dtype);
+    e = launch_ypass<T>(y, false, ygrid, yblock, ysm, s);
+    if (e != cudaSuccess) return cuda_fail(e, "y forward pass");
+    mark(2);
+
+    XArgs<T> x{};
+    x.data = ui;
+    x.batch = g.count;
+    x.nx = g.nx;
+    x.ny = g.ny;
+    x.M = g.M;
+    x.sInst = (long long)g.nx * g.ny * g.M;
+    x.W = g.Wx;
+    x.ncb = (g.M + g.Wx - 1) / g.Wx;
+    x.main_tiles = (long long)g.count * g.ny * x.ncb;
+    x.npairs = (long long)g.count * (g.ny / 2 + 1);
+    x.pl = g.px;
+    x.tw = tab + g.tw_x;
+    const double N = (double)g.nx * g.ny * g.nz;
+    x.coef = (T)(1.0 / (4.0 * M_PI * M_PI * N));
+    const unsigned xgrid = (unsigned)(x.main_tiles + (x.npairs + g.Wx / 2 - 1) / (g.Wx / 2));
+    const unsigned xblock = (unsigned)(g.Wx * g.px.TL);
+    e = launch_xfused<T>(x, xgrid, xblock, s_smem(g.nx, g.Wx, dtype), s);
+    if (e != cudaSuccess) return cuda_fail(e, "x pass with spectral division");
+    mark(3);
+
+    e = launch_ypass<T>(y, true, ygrid, yblock, ysm, s);
+    if (e != cudaSuccess) return cuda_fail(e, "y inverse pass");
+    mark(4);
+
+    ZArgs<T> zi = z;
+    zi.in = ui;
+    zi.out = ui;
+    e = launch_zinv<T>(zi, zgrid, zblock, z_smem(g, dtype), s);
+    if (e != cudaSuccess) return cuda_fail(e, "z inverse pass");
+    mark(5);
+    return PSOLVE_OK;
+}
+
+psolve_status check_buffers(const psolve_plan *p, const void *f, const void *u)
+{
+    if (!f || !u) return fail(PSOLVE_ERR_INVALID_ARG, "null array pointer");
+    if (((uintptr_t)f & 15) || ((uintptr_t)u & 15))
+        return fail(PSOLVE_ERR_INVALID_ARG, "arrays must be 16-byte aligned");
+    if (f != u) {
+        const uintptr_t a0 = (uintptr_t)f, b0 = (uintptr_t)u;
+        const uintptr_t len = (uintptr_t)(p->total * rsize(p->dtype));
+        if (a0 < b0 + len && b0 < a0 + len) return fail(PSOLVE_ERR_INVALID_ARG, "f and u partially overlap");
+    }
+    return PSOLVE_OK;
+}
+
+psolve_status solve(psolve_plan *p, const void *f, void *u, void *stream)
+{
+    if (!plan_ok(p)) return fail(PSOLVE_ERR_INVALID_ARG, "invalid or destroyed plan");
+    psolve_status st = check_buffers(p, f, u);
+    if (st != PSOLVE_OK) return st;
+    DeviceGuard dg(p->device);
+    if (dg.err != cudaSuccess) return cuda_fail(dg.err, "select device");
+    cudaStream_t s = (cudaStream_t)stream;
+    for (const auto &g : p->groups) {
+        const std::vector<cudaEvent_t> *ev = take_events(p);
+        st = p->dtype == PSOLVE_F64
+                 ? run_group<double>(p, g, (const double *)f, (double *)u, s, ev)
+                 : run_group<float>(p, g, (const float *)f, (float *)u, s, ev);
+        if (st != PSOLVE_OK) return st;
+    }
+    return PSOLVE_OK;
+}
+
+std::mutex g_norm_mu;
+double *g_norm_buf[64] = {nullptr};
+
+} // namespace
+
+extern "C" {
+
+psolve_status psolve_plan_create(int nx, int ny, int nz, int dtype, int batch, psolve_plan **out)
+{
+    if (!out) return fail(PSOLVE_ERR_INVALID_ARG, "out is null");
+    *out = nullptr;
+    if (dtype != PSOLVE_F64 && dtype != PSOLVE_F32 && dtype != PSOLVE_F32_TC)
+        return fail(PSOLVE_ERR_INVALID_ARG, "unknown dtype");
+    if (dtype == PSOLVE_F32_TC)
+        return fail(PSOLVE_ERR_INVALID_ARG, "tensor-core precision is not built in this version");
+    if (batch < 1) return fail(PSOLVE_ERR_INVALID_ARG, "batch must be >= 1");
+    if (!size_ok(nx) || !size_ok(ny) || !size_ok(nz))
+        return fail(PSOLVE_ERR_UNSUPPORTED_SIZE, "each n must be 2^a 3^b, even, 4 <= n <= 2048");
+    std::vector<int> X(batch, nx), Y(batch, ny), Z(batch, nz);
+    return build_plan(X, Y, Z, dtype, true, out);
+}
+
+psolve_status psolve_plan_create_many(const int *nx, const int *ny, const int *nz, int batch, int dtype,
+                                      psolve_plan **out)
+{
+    if (!out) return fail(PSOLVE_ERR_INVALID_ARG, "out is null");
+    *out = nullptr;
+    if (!nx || !ny || !nz) return fail(PSOLVE_ERR_INVALID_ARG, "null size array");
+    if (dtype != PSOLVE_F64 && dtype != PSOLVE_F32 && dtype != PSOLVE_F32_TC)
+        return fail(PSOLVE_ERR_INVALID_ARG, "unknown dtype");
+    if (dtype == PSOLVE_F32_TC)
+        return fail(PSOLVE_ERR_INVALID_ARG, "tensor-core precision is not built in this version");
+    if (batch < 1) return fail(PSOLVE_ERR_INVALID_ARG, "batch must be >= 1");
+    std::vector<int> X(nx, nx + batch), Y(ny, ny + batch), Z(nz, nz + batch);
+    for (int b = 0; b < batch; ++b)
+        if (!size_ok(X[b]) || !size_ok(Y[b]) || !size_ok(Z[b]))
+            return fail(PSOLVE_ERR_UNSUPPORTED_SIZE, "instance " + std::to_string(b) +
+                                                         ": each n must be 2^a 3^b, even, 4 <= n <= 2048");
+    return build_plan(X, Y, Z, dtype, false, out);
+}
+
+psolve_status psolve_execute(psolve_plan *plan, const void *f, void *u, void *stream)
+{
+    return solve(plan, f, u, stream);
+}
+
+psolve_status psolve_adjoint(psolve_plan *plan, const void *g, void *grad_f, void *stream)
+{
+    // A = F^{-1} D F with D real and even in k is symmetric: A^T = A.
+    return solve(plan, g, grad_f, stream);
+}
+
+psolve_status psolve_execute_host(psolve_plan *plan, const void *f_host, void *u_host, void *stream)
+{
+    if (!plan_ok(plan)) return fail(PSOLVE_ERR_INVALID_ARG, "invalid or destroyed plan");
+    if (!f_host || !u_host) return fail(PSOLVE_ERR_INVALID_ARG, "null host pointer");
+    DeviceGuard dg(plan->device);
+    if (dg.err != cudaSuccess) return cuda_fail(dg.err, "select device");
+    const size_t bytes = plan->total * rsize(plan->dtype);
+    if (plan->stage_bytes < bytes) {
+        if (plan->stage) cudaFree(plan->stage);
+        plan->stage = nullptr;
+        plan->stage_bytes = 0;
+        if (cudaMalloc(&plan->stage, bytes) != cudaSuccess) {
+            plan->stage = nullptr;
+            return fail(PSOLVE_ERR_OOM, "device staging buffer: cudaMalloc failed");
+        }
+        plan->stage_bytes = bytes;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaMemcpyAsync(plan->stage, f_host, bytes, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(e, "copy f to device");
+    psolve_status st = solve(plan, plan->stage, plan->stage, stream);
+    if (st != PSOLVE_OK) return st;
+    e = cudaMemcpyAsync(u_host, plan->stage, bytes, cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return cuda_fail(e, "copy u to host");
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "synchronise stream");
+    return PSOLVE_OK;
+}
+
+psolve_status psolve_destroy(psolve_plan *plan)
+{
+    if (!plan_ok(plan)) return fail(PSOLVE_ERR_INVALID_ARG, "invalid or destroyed plan");
+    DeviceGuard dg(plan->device);
+    release(plan);
+    return PSOLVE_OK;
+}
+
+size_t psolve_instance_offset(const psolve_plan *plan, int b)
+{
+    if (!plan_ok(plan) || b < 0 || b >= plan->batch) return (size_t)-1;
+    return plan->inst_off[b];
+}
+
+size_t psolve_total_elements(const psolve_plan *plan)
+{
+    if (!plan_ok(plan)) return 0;
+    return plan->total;
+}
+
+psolve_status psolve_get_status(psolve_plan *plan, void *stream)
+{
+    if (!plan_ok(plan)) return fail(PSOLVE_ERR_INVALID_ARG, "invalid or destroyed plan");
+    DeviceGuard dg(plan->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "synchronise stream");
+    int word = 0;
+    e = cudaMemcpy(&word, plan->status, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "read status word");
+    cudaMemset(plan->status, 0, sizeof(int));
+    if (word == 0) return PSOLVE_OK;
+    if (word == PSOLVE_ERR_TIMEOUT) return fail(PSOLVE_ERR_TIMEOUT, "a device-side wait gave up");
+    return fail(PSOLVE_ERR_INTERNAL, "device status word " + std::to_string(word));
+}
+
+psolve_status psolve_debug_kvec(const psolve_plan *plan, int b, int *kxyz_out)
+{
+    if (!plan_ok(plan)) return fail(PSOLVE_ERR_INVALID_ARG, "invalid or destroyed plan");
+    if (b < 0 || b >= plan->batch || !kxyz_out) return fail(PSOLVE_ERR_INVALID_ARG, "bad instance or buffer");
+    const Group &g = plan->groups[plan->groups.size() == 1 ? 0 : b];
+    DeviceGuard dg(plan->device);
+    const size_t n = (size_t)g.nx * g.ny * (g.nz / 2 + 1) * 3;
+    int *d = nullptr;
+    if (cudaMalloc(&d, n * sizeof(int)) != cudaSuccess) return fail(PSOLVE_ERR_OOM, "kvec buffer");
+    cudaError_t e = launch_kvec(d, g.nx, g.ny, g.nz, 0);
+    if (e == cudaSuccess) e = cudaMemcpy(kxyz_out, d, n * sizeof(int), cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (e != cudaSuccess) return cuda_fail(e, "kvec export");
+    return PSOLVE_OK;
+}
+
+psolve_status psolve_error_norms(const void *a, const void *ref, size_t n, int dtype, double *out4, void *stream)
+{
+    if (!a || !ref || !out4) return fail(PSOLVE_ERR_INVALID_ARG, "null pointer");
+    if (dtype != PSOLVE_F64 && dtype != PSOLVE_F32 && dtype != PSOLVE_F32_TC)
+        return fail(PSOLVE_ERR_INVALID_ARG, "unknown dtype");
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (dev < 0 || dev >= 64) return fail(PSOLVE_ERR_INVALID_ARG, "device index out of range");
+    std::lock_guard<std::mutex> lk(g_norm_mu);
+    if (!g_norm_buf[dev]) {
+        if (cudaMalloc((void **)&g_norm_buf[dev], 4 * sizeof(double)) != cudaSuccess) {
+            g_norm_buf[dev] = nullptr;
+            return fail(PSOLVE_ERR_OOM, "norm buffer");
+        }
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    double *buf = g_norm_buf[dev];
+    e = cudaMemsetAsync(buf, 0, 4 * sizeof(double), s);
+    if (e == cudaSuccess)
+        e = dtype == PSOLVE_F64 ? launch_norms<double>((const double *)a, (const double *)ref, n, buf, s)
+                                : launch_norms<float>((const float *)a, (const float *)ref, n, buf, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out4, buf, 4 * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "error norms");
+    return PSOLVE_OK;
+}
+
+psolve_status psolve_set_profiling(psolve_plan *plan, int enable)
+{
+    if (!plan_ok(plan)) return fail(PSOLVE_ERR_INVALID_ARG, "invalid or destroyed plan");
+    plan->profiling = enable != 0;
+    return PSOLVE_OK;
+}
+
+psolve_status psolve_pass_times(psolve_plan *plan, double *ms, int cap, int *n_passes, int *n_solves)
+{
+    if (!plan_ok(plan)) return fail(PSOLVE_ERR_INVALID_ARG, "invalid or destroyed plan");
+    if (!ms || cap < 0) return fail(PSOLVE_ERR_INVALID_ARG, "null output");
+    DeviceGuard dg(plan->device);
+    for (int i = 0; i < cap; ++i) ms[i] = 0.0;
+    int solves = 0;
+    for (auto &set : plan->ev_used) {
+        cudaError_t e = cudaEventSynchronize(set[kPasses]);
+        if (e != cudaSuccess) return cuda_fail(e, "profiling events");
+        for (int i = 0; i < kPasses && i < cap; ++i) {
+            float t = 0.f;
+            e = cudaEventElapsedTime(&t, set[i], set[i + 1]);
+            if (e != cudaSuccess) return cuda_fail(e, "profiling events");
+            ms[i] += t;
+        }
+        ++solves;
+    }
+    for (auto &set : plan->ev_used) plan->ev_free.push_back(std::move(set));
+    plan->ev_used.clear();
+    if (n_passes) *n_passes = kPasses;
+    if (n_solves) *n_solves = solves;
+    return PSOLVE_OK;
+}
+
+const char *psolve_pass_name(const psolve_plan *plan, int i)
+{
+    if (!plan_ok(plan) || i < 0 || i >= kPasses) return nullptr;
+    return kPassNames[i];
+}
+
+int psolve_launches_per_solve(const psolve_plan *plan)
+{
+    if (!plan_ok(plan)) return 0;
+    return kPasses * (int)plan->groups.size();
+}
+
+const char *psolve_status_string(psolve_status s)
+{
+    switch (s) {
+    case PSOLVE_OK: return "ok";
+    case PSOLVE_ERR_INVALID_ARG: return "invalid argument";
+    case PSOLVE_ERR_UNSUPPORTED_SIZE: return "unsupported size";
+    case PSOLVE_ERR_OOM: return "out of device memory";
+    case PSOLVE_ERR_CUDA: return "CUDA error";
+    case PSOLVE_ERR_TIMEOUT: return "device-side wait timed out";
+    case PSOLVE_ERR_INTERNAL: return "internal error";
+    }
+    return "unknown status";
+}
+
+const char *psolve_last_error(void) { return g_last_error.c_str(); }
+
+int psolve_version(void) { return 100; }
+
+} // extern "C"

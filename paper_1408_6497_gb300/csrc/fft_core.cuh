@@ -1,0 +1,292 @@
+// Register/shared-memory FFT engine shared by every pass kernel.
+//
+// A line of L complex points is processed by TL = L/E threads, each holding
+// E points in registers.  Thread t starts and ends holding the "strided
+// class" of the line: v[m] = x[t + m·TL], m = 0..E-1.  The transform is a
+// mixed-radix Stockham (self-sorting) FFT: stage s with radix R and
+// Ns = R_1·…·R_{s-1} takes butterfly j (0 <= j < L/R) over the inputs
+// x[j + r·L/R], multiplies input r by w_{Ns·R}^{r·(j mod Ns)}, applies the
+// R-point DFT and writes output k to y[(j / Ns)·Ns·R + (j mod Ns) + k·Ns].
+// Thread t owns butterflies j = t + b·TL (b < E/R), whose inputs are exactly
+// v[b + r·E/R], so only the outputs go through shared memory; the last stage
+// (Ns·R = L) writes back into the strided class, i.e. stays in registers.
+// This is the 1D building block of the 3D transform in §2.1.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace psolve {
+
+template <typename T> struct cplx_of;
+template <> struct cplx_of<float> { using type = float2; };
+template <> struct cplx_of<double> { using type = double2; };
+
+template <typename C> __device__ __forceinline__ C cadd(C a, C b) { return {a.x + b.x, a.y + b.y}; }
+template <typename C> __device__ __forceinline__ C csub(C a, C b) { return {a.x - b.x, a.y - b.y}; }
+template <typename C> __device__ __forceinline__ C cmul(C a, C b)
+{
+    return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+}
+// a · conj(b)
+template <typename C> __device__ __forceinline__ C cmulc(C a, C b)
+{
+    return {a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y};
+}
+template <typename C, typename S> __device__ __forceinline__ C cscale(C a, S s) { return {a.x * s, a.y * s}; }
+template <typename C> __device__ __forceinline__ C cconj(C a) { return {a.x, -a.y}; }
+
+// Multiply by -i (forward direction) or +i (inverse direction).
+template <bool INV, typename C> __device__ __forceinline__ C rot90(C a)
+{
+    return INV ? C{-a.y, a.x} : C{a.y, -a.x};
+}
+
+// Exact values of cos(πm/8), sin(πm/8), m = 0..8, for the radix-8/16 kernels.
+struct Oct {
+    static constexpr double c[9] = {1.0,
+                                    0.923879532511286756128183189396788933,
+                                    0.707106781186547524400844362104849039,
+                                    0.382683432365089771728459984030398866,
+                                    0.0,
+                                    -0.382683432365089771728459984030398866,
+                                    -0.707106781186547524400844362104849039,
+                                    -0.923879532511286756128183189396788933,
+                                    -1.0};
+    static constexpr double s[9] = {0.0,
+                                    0.382683432365089771728459984030398866,
+                                    0.707106781186547524400844362104849039,
+                                    0.923879532511286756128183189396788933,
+                                    1.0,
+                                    0.923879532511286756128183189396788933,
+                                    0.707106781186547524400844362104849039,
+                                    0.382683432365089771728459984030398866,
+                                    0.0};
+};
+
+// a · w_16^m with w_16 = e^{∓2πi/16} (forward/inverse), 0 <= m <= 8.
+template <bool INV, int M, typename C> __device__ __forceinline__ C mul_w16(C a)
+{
+    using T = decltype(a.x);
+    if constexpr (M == 0) {
+        return a;
+    } else if constexpr (M == 4) {
+        return rot90<INV>(a);
+    } else if constexpr (M == 8) {
+        return C{-a.x, -a.y};
+    } else {
+        const T c = (T)Oct::c[M];
+        const T s = INV ? (T)Oct::s[M] : -(T)Oct::s[M];
+        return C{a.x * c - a.y * s, a.x * s + a.y * c};
+    }
+}
+
+// ---------------------------------------------------------------- butterflies
+// In-place R-point DFT  a[k] <- Σ_r a[r] e^{∓2πi rk/R}.
+
+template <bool INV, typename C> __device__ __forceinline__ void dft2(C *a)
+{
+    C t = a[0];
+    a[0] = cadd(t, a[1]);
+    a[1] = csub(t, a[1]);
+}
+
+template <bool INV, typename C> __device__ __forceinline__ void dft3(C *a)
+{
+    using T = decltype(a[0].x);
+    const T h = (T)0.866025403784438646763723170752936183; // √3/2
+    C t1 = cadd(a[1], a[2]);
+    C t2 = csub(a[1], a[2]);
+    C m = {a[0].x - (T)0.5 * t1.x, a[0].y - (T)0.5 * t1.y};
+    a[0] = cadd(a[0], t1);
+    // forward: out1 = m - i h t2, out2 = m + i h t2
+    C r = {h * t2.y, -h * t2.x}; // -i h t2
+    if (INV) r = C{-r.x, -r.y};
+    a[1] = cadd(m, r);
+    a[2] = csub(m, r);
+}
+
+template <bool INV, typename C> __device__ __forceinline__ void dft4(C *a)
+{
+    C a0 = cadd(a[0], a[2]), a1 = csub(a[0], a[2]);
+    C a2 = cadd(a[1], a[3]), a3 = rot90<INV>(csub(a[1], a[3]));
+    a[0] = cadd(a0, a2);
+    a[2] = csub(a0, a2);
+    a[1] = cadd(a1, a3);
+    a[3] = csub(a1, a3);
+}
+
+template <bool INV, typename C> __device__ __forceinline__ void dft8(C *a)
+{
+    C e[4] = {a[0], a[2], a[4], a[6]};
+    C o[4] = {a[1], a[3], a[5], a[7]};
+    dft4<INV>(e);
+    dft4<INV>(o);
+    o[1] = mul_w16<INV, 2>(o[1]);
+    o[2] = mul_w16<INV, 4>(o[2]);
+    o[3] = mul_w16<INV, 6>(o[3]);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        a[k] = cadd(e[k], o[k]);
+        a[k + 4] = csub(e[k], o[k]);
+    }
+}
+
+// 16 = 4 × 4:  n = 4 n1 + n2,  k = k1 + 4 k2.
+template <bool INV, typename C> __device__ __forceinline__ void dft16(C *a)
+{
+    C y[4][4]; // y[n2][k1]
+#pragma unroll
+    for (int n2 = 0; n2 < 4; ++n2) {
+        C col[4] = {a[n2], a[4 + n2], a[8 + n2], a[12 + n2]};
+        dft4<INV>(col);
+#pragma unroll
+        for (int k1 = 0; k1 < 4; ++k1) y[n2][k1] = col[k1];
+    }
+    // twiddles w16^{n2·k1}
+    y[1][1] = mul_w16<INV, 1>(y[1][1]);
+    y[1][2] = mul_w16<INV, 2>(y[1][2]);
+    y[1][3] = mul_w16<INV, 3>(y[1][3]);
+    y[2][1] = mul_w16<INV, 2>(y[2][1]);
+    y[2][2] = mul_w16<INV, 4>(y[2][2]);
+    y[2][3] = mul_w16<INV, 6>(y[2][3]);
+    y[3][1] = mul_w16<INV, 3>(y[3][1]);
+    y[3][2] = mul_w16<INV, 6>(y[3][2]);
+    {
+        // w16^9 = -w16^1
+        C t = mul_w16<INV, 1>(y[3][3]);
+        y[3][3] = C{-t.x, -t.y};
+    }
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) {
+        C row[4] = {y[0][k1], y[1][k1], y[2][k1], y[3][k1]};
+        dft4<INV>(row);
+#pragma unroll
+        for (int k2 = 0; k2 < 4; ++k2) a[k1 + 4 * k2] = row[k2];
+    }
+}
+
+template <int R, bool INV, typename C> __device__ __forceinline__ void dft(C *a)
+{
+    if constexpr (R == 2) dft2<INV>(a);
+    else if constexpr (R == 3) dft3<INV>(a);
+    else if constexpr (R == 4) dft4<INV>(a);
+    else if constexpr (R == 8) dft8<INV>(a);
+    else if constexpr (R == 16) dft16<INV>(a);
+}
+
+// ------------------------------------------------------------------ plans
+
+constexpr int kMaxStages = 16;
+
+// One 1D transform of length L split into stages; computed on the host.
+struct LinePlan {
+    int L;                      // line length (complex points)
+    int E;                      // points per thread
+    int TL;                     // threads per line = L / E
+    int nst;                    // number of stages
+    int radix[kMaxStages];      // R_s
+    int ns[kMaxStages];         // Ns before stage s
+    int twstep[kMaxStages];     // L / (Ns·R): twiddle index step
+};
+
+// Index map of a line's point p into the shared exchange buffer.
+struct MapStrided { // [p][w], pitch P: lines side by side (y and x passes)
+    int P, w;
+    __device__ __forceinline__ int operator()(int p) const { return p * P + w; }
+};
+struct MapRow { // [w][p], one padded row per line (z passes)
+    int base;
+    __device__ __forceinline__ int operator()(int p) const { return base + p + (p >> 4); }
+};
+
+template <int R, bool INV, bool LAST, int E, typename C, typename Map>
+__device__ __forceinline__ void fft_stage(C (&v)[E], int t, int TL, int Ns, int twstep,
+                                          const C *__restrict__ tw, C *sm, const Map &map,
+                                          bool active)
+{
+    constexpr int NB = E / R;
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+        const int j = t + b * TL;
+        const int jm = j % Ns;
+        C a[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) a[r] = v[b + r * NB];
+        if (Ns > 1) {
+            const int q = jm * twstep;
+#pragma unroll
+            for (int r = 1; r < R; ++r) {
+                const C w = tw[r * q];
+                a[r] = INV ? cmulc(a[r], w) : cmul(a[r], w);
+            }
+        }
+        dft<R, INV>(a);
+        if constexpr (LAST) {
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[b + r * NB] = a[r];
+        } else {
+            if (active) {
+                const int base = (j - jm) * R + jm;
+#pragma unroll
+                for (int r = 0; r < R; ++r) sm[map(base + r * Ns)] = a[r];
+            }
+        }
+    }
+}
+
+template <int R, int E> struct RadixOk { static constexpr bool value = (E % R) == 0; };
+
+template <bool INV, bool LAST, int E, typename C, typename Map>
+__device__ __forceinline__ void fft_stage_dispatch(int R, C (&v)[E], int t, int TL, int Ns, int twstep,
+                                                   const C *__restrict__ tw, C *sm, const Map &map,
+                                                   bool active)
+{
+    switch (R) {
+    case 16:
+        if constexpr (RadixOk<16, E>::value) fft_stage<16, INV, LAST>(v, t, TL, Ns, twstep, tw, sm, map, active);
+        break;
+    case 8:
+        if constexpr (RadixOk<8, E>::value) fft_stage<8, INV, LAST>(v, t, TL, Ns, twstep, tw, sm, map, active);
+        break;
+    case 4:
+        if constexpr (RadixOk<4, E>::value) fft_stage<4, INV, LAST>(v, t, TL, Ns, twstep, tw, sm, map, active);
+        break;
+    case 3:
+        if constexpr (RadixOk<3, E>::value) fft_stage<3, INV, LAST>(v, t, TL, Ns, twstep, tw, sm, map, active);
+        break;
+    case 2:
+        if constexpr (RadixOk<2, E>::value) fft_stage<2, INV, LAST>(v, t, TL, Ns, twstep, tw, sm, map, active);
+        break;
+    default:
+        break;
+    }
+}
+
+// Full line transform.  All threads of the block must call it (it contains
+// __syncthreads); `active` masks the shared-memory writes of idle threads.
+template <bool INV, int E, typename C, typename Map>
+__device__ __forceinline__ void line_fft(C (&v)[E], int t, const LinePlan &pl,
+                                         const C *__restrict__ tw, C *sm, const Map &map, bool active)
+{
+    for (int s = 0; s < pl.nst; ++s) {
+        const int R = pl.radix[s];
+        if (s + 1 == pl.nst) {
+            fft_stage_dispatch<INV, true>(R, v, t, pl.TL, pl.ns[s], pl.twstep[s], tw, sm, map, active);
+        } else {
+            fft_stage_dispatch<INV, false>(R, v, t, pl.TL, pl.ns[s], pl.twstep[s], tw, sm, map, active);
+            __syncthreads();
+            if (active) {
+#pragma unroll
+                for (int m = 0; m < E; ++m) v[m] = sm[map(t + m * pl.TL)];
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// Signed wavenumber of index j on an axis of n points: j for j <= n/2,
+// j - n otherwise (the Nyquist index counts as +n/2).
+__device__ __forceinline__ int kvec_dev(int j, int n) { return (2 * j <= n) ? j : j - n; }
+
+} // namespace psolve

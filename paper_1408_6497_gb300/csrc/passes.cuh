@@ -1,0 +1,306 @@
+// The five pass kernels of one solve (§2.1, §3: forward 3D FFT, diagonal
+// scaling by the inverse Laplacian symbol, inverse 3D FFT), as templates over
+// the precision T and the points-per-thread E.
+//
+// Data layout.  f and u are real (nx, ny, nz), z contiguous.  The half
+// spectrum is formed inside u's own bytes as complex S[x][y][kz],
+// 0 <= kz < M = nz/2: a row of nz reals and a row of M complex values have
+// the same size, so every pass works in place and no workspace of the grid's
+// size exists.  The z-Nyquist coefficient X[M] of a real z-line is real, as
+// is X[0]; the pair is packed into slot 0 as X[0] + i·X[M].  The y and x
+// transforms act linearly on that packed column, and the x-pass separates
+// the two real-signal spectra with the mirror row (-ky) before scaling them.
+//
+//   zfwd   : real rows -> packed complex rows (M-point FFT + split post-twiddle)
+//   ypass  : c2c along y, tiles of W adjacent kz-columns at fixed x
+//   xfused : c2c along x, scale by 1/(4π²|k|²N), inverse c2c along x; extra
+//            blocks handle the packed kz = 0 / kz = M column pairs
+//   zinv   : packed complex rows -> real rows (pre-twiddle + M-point FFT)
+#pragma once
+
+#include "fft_core.cuh"
+
+namespace psolve {
+
+template <typename T> struct ZArgs {
+    using C = typename cplx_of<T>::type;
+    const T *in;      // zfwd: f;  zinv: packed spectrum
+    T *out;           // zfwd: packed spectrum;  zinv: u
+    long long rows;   // lines of nz reals
+    int nz, M, W;     // W rows per block
+    LinePlan pl;      // L = M
+    const C *tw;      // e^{-2πi j/M}, j < M
+    const C *post;    // e^{-2πi k/nz}, k < M
+};
+
+template <typename T> struct SArgs {
+    using C = typename cplx_of<T>::type;
+    T *data;          // packed spectrum
+    long long nplanes;
+    long long sPlane; // complex elements between planes
+    long long sL;     // complex elements between points of a line
+    int M, W, ncb;    // columns per row, columns per tile, tiles per plane
+    LinePlan pl;
+    const C *tw;
+};
+
+template <typename T> struct XArgs {
+    using C = typename cplx_of<T>::type;
+    T *data;
+    int batch, nx, ny, M;
+    long long sInst;     // complex elements between instances
+    int W, ncb;
+    long long main_tiles;
+    long long npairs;    // batch · (ny/2 + 1)
+    LinePlan pl;         // L = nx
+    const C *tw;
+    T coef;              // 1 / (4π² N), N = nx·ny·nz
+};
+
+// Launch bound per instantiation: the host mirrors this in max_threads().
+template <typename T, int E> struct Bound {
+    static constexpr int value = (sizeof(T) == 8 || E > 16) ? 256 : 512;
+};
+
+// --------------------------------------------------------------- z forward
+template <typename T, int E>
+__global__ void __launch_bounds__(Bound<T, E>::value) k_zfwd(ZArgs<T> a)
+{
+    using C = typename cplx_of<T>::type;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    C *stw = reinterpret_cast<C *>(smraw);
+    C *sx = stw + a.M;
+    const int TL = a.pl.TL;
+    const int tid = threadIdx.x;
+    const int w = tid / TL, t = tid - w * TL;
+    const long long row = (long long)blockIdx.x * a.W + w;
+    const bool active = (w < a.W) && (row < a.rows);
+    for (int i = tid; i < a.M; i += blockDim.x) stw[i] = a.tw[i];
+    C v[E];
+    if (active) {
+        const C *src = reinterpret_cast<const C *>(a.in + row * a.nz) + t;
+#pragma unroll
+        for (int m = 0; m < E; ++m) v[m] = src[m * TL];
+    } else {
+#pragma unroll
+        for (int m = 0; m < E; ++m) v[m] = C{0, 0};
+    }
+    __syncthreads();
+    const int LP = a.M + (a.M >> 4) + 1;
+    const MapRow map{w * LP};
+    line_fft<false>(v, t, a.pl, stw, sx, map, active);
+    // Z[k] -> X[k] needs Z[M-k]: exchange through shared memory.
+    if (active) {
+#pragma unroll
+        for (int m = 0; m < E; ++m) sx[map(t + m * TL)] = v[m];
+    }
+    __syncthreads();
+    if (active) {
+        C *dst = reinterpret_cast<C *>(a.out) + row * a.M;
+        const T half = (T)0.5;
+#pragma unroll
+        for (int m = 0; m < E; ++m) {
+            const int k = t + m * TL;
+            const C z = v[m];
+            if (k == 0) {
+                dst[0] = C{z.x + z.y, z.x - z.y}; // X[0] + i X[M]
+            } else {
+                const C zp = sx[map(a.M - k)];
+                const C e = {(z.x + zp.x) * half, (z.y - zp.y) * half};   // (Z + conj Zp)/2
+                const C o = {(z.y + zp.y) * half, (zp.x - z.x) * half};   // (Z - conj Zp)/(2i)
+                dst[k] = cadd(e, cmul(o, a.post[k]));
+            }
+        }
+    }
+}
+
+// --------------------------------------------------------------- z inverse
+template <typename T, int E>
+__global__ void __launch_bounds__(Bound<T, E>::value) k_zinv(ZArgs<T> a)
+{
+    using C = typename cplx_of<T>::type;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    C *stw = reinterpret_cast<C *>(smraw);
+    C *sx = stw + a.M;
+    const int TL = a.pl.TL;
+    const int tid = threadIdx.x;
+    const int w = tid / TL, t = tid - w * TL;
+    const long long row = (long long)blockIdx.x * a.W + w;
+    const bool active = (w < a.W) && (row < a.rows);
+    for (int i = tid; i < a.M; i += blockDim.x) stw[i] = a.tw[i];
+    C v[E];
+    if (active) {
+        const C *src = reinterpret_cast<const C *>(a.in) + row * a.M;
+#pragma unroll
+        for (int m = 0; m < E; ++m) {
+            const int k = t + m * TL;
+            const C x = src[k];
+            if (k == 0) {
+                v[m] = C{x.x + x.y, x.x - x.y};
+            } else {
+                const C xp = src[a.M - k];
+                const C e = {x.x + xp.x, x.y - xp.y};                  // X + conj Xp
+                const C o = cmulc(C{x.x - xp.x, x.y + xp.y}, a.post[k]); // (X - conj Xp) e^{+2πik/nz}
+                v[m] = C{e.x - o.y, e.y + o.x};                        // E + i O
+            }
+        }
+    } else {
+#pragma unroll
+        for (int m = 0; m < E; ++m) v[m] = C{0, 0};
+    }
+    __syncthreads(); // every load of the row precedes any store (in place)
+    const int LP = a.M + (a.M >> 4) + 1;
+    const MapRow map{w * LP};
+    line_fft<true>(v, t, a.pl, stw, sx, map, active);
+    if (active) {
+        C *dst = reinterpret_cast<C *>(a.out + row * a.nz) + t;
+#pragma unroll
+        for (int m = 0; m < E; ++m) dst[m * TL] = v[m];
+    }
+}
+
+// ------------------------------------------------------- strided c2c (y)
+template <typename T, int E, bool INV>
+__global__ void __launch_bounds__(Bound<T, E>::value) k_ypass(SArgs<T> a)
+{
+    using C = typename cplx_of<T>::type;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    C *stw = reinterpret_cast<C *>(smraw);
+    C *sx = stw + a.pl.L;
+    const int W = a.W, TL = a.pl.TL;
+    const int tid = threadIdx.x;
+    const int w = tid % W, t = tid / W;
+    const long long tile = blockIdx.x;
+    const int cb = (int)(tile % a.ncb);
+    const long long plane = tile / a.ncb;
+    const int col = cb * W + w;
+    const bool active = col < a.M;
+    for (int i = tid; i < a.pl.L; i += blockDim.x) stw[i] = a.tw[i];
+    C *base = reinterpret_cast<C *>(a.data) + plane * a.sPlane + col + (long long)t * a.sL;
+    const long long step = (long long)TL * a.sL;
+    C v[E];
+    if (active) {
+#pragma unroll
+        for (int m = 0; m < E; ++m) v[m] = base[m * step];
+    } else {
+#pragma unroll
+        for (int m = 0; m < E; ++m) v[m] = C{0, 0};
+    }
+    __syncthreads();
+    const MapStrided map{W, w};
+    line_fft<INV>(v, t, a.pl, stw, sx, map, active);
+    if (active) {
+#pragma unroll
+        for (int m = 0; m < E; ++m) base[m * step] = v[m];
+    }
+}
+
+// ----------------------------------- x forward, spectral division, x inverse
+template <typename T, int E>
+__global__ void __launch_bounds__(Bound<T, E>::value) k_xfused(XArgs<T> a)
+{
+    using C = typename cplx_of<T>::type;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    C *stw = reinterpret_cast<C *>(smraw);
+    C *sx = stw + a.pl.L;
+    const int W = a.W, TL = a.pl.TL, nx = a.nx, ny = a.ny, M = a.M;
+    const int tid = threadIdx.x;
+    const int w = tid % W, t = tid / W;
+    const long long tile = blockIdx.x;
+    const long long sL = (long long)ny * M;
+    const long long step = (long long)TL * sL;
+    for (int i = tid; i < nx; i += blockDim.x) stw[i] = a.tw[i];
+    const MapStrided map{W, w};
+    C v[E];
+
+    if (tile < a.main_tiles) {
+        const int cb = (int)(tile % a.ncb);
+        const long long rest = tile / a.ncb;
+        const int y = (int)(rest % ny);
+        const long long b = rest / ny;
+        const int col = cb * W + w;
+        const bool active = col < M;
+        C *base = reinterpret_cast<C *>(a.data) + b * a.sInst + (long long)y * M + col + (long long)t * sL;
+        if (active) {
+#pragma unroll
+            for (int m = 0; m < E; ++m) v[m] = base[m * step];
+        } else {
+#pragma unroll
+            for (int m = 0; m < E; ++m) v[m] = C{0, 0};
+        }
+        __syncthreads();
+        line_fft<false>(v, t, a.pl, stw, sx, map, active);
+        const int ky = kvec_dev(y, ny);
+        const int kyz = ky * ky + col * col;
+#pragma unroll
+        for (int m = 0; m < E; ++m) {
+            const int kx = kvec_dev(t + m * TL, nx);
+            const int k2 = kx * kx + kyz;
+            const T d = (k2 == 0) ? (T)0 : a.coef / (T)k2;
+            v[m] = cscale(v[m], d);
+        }
+        line_fft<true>(v, t, a.pl, stw, sx, map, active);
+        if (active && col != 0) {
+#pragma unroll
+            for (int m = 0; m < E; ++m) base[m * step] = v[m];
+        }
+        return;
+    }
+
+    // Packed column kz = 0 holds X0 + i·XM for every (x, y) line.  After the
+    // 2D (y, x) transform H = G0 + i·G1 with G0, G1 the spectra of two real
+    // planes, so G0(k) = (H(k) + conj H(-k))/2, G1(k) = (H(k) - conj H(-k))/(2i).
+    // Each is scaled by its own symbol (kz = 0 and kz = M) and recombined:
+    //   H'(k) = ((D0 + D1)/2) H(k) + ((D0 - D1)/2) conj H(-k).
+    // Lines 2q and 2q+1 of the block hold rows ky and (ny - ky) mod ny.
+    const long long pidx = tile - a.main_tiles;
+    const int half = W >> 1;
+    const int q = w >> 1, side = w & 1;
+    const long long pair = pidx * half + q;
+    const bool active = (w < 2 * half) && (pair < a.npairs);
+    const int per = ny / 2 + 1;
+    const long long b = active ? pair / per : 0;
+    const int ky = active ? (int)(pair % per) : 0;
+    const int row = side ? (ny - ky) % ny : ky;
+    C *base = reinterpret_cast<C *>(a.data) + b * a.sInst + (long long)row * M + (long long)t * sL;
+    if (active) {
+#pragma unroll
+        for (int m = 0; m < E; ++m) v[m] = base[m * step];
+    } else {
+#pragma unroll
+        for (int m = 0; m < E; ++m) v[m] = C{0, 0};
+    }
+    __syncthreads();
+    line_fft<false>(v, t, a.pl, stw, sx, map, active);
+    if (active) {
+#pragma unroll
+        for (int m = 0; m < E; ++m) sx[map(t + m * TL)] = v[m];
+    }
+    __syncthreads();
+    if (active) {
+        const int kys = kvec_dev(row, ny);
+        const int partner = w ^ 1;
+#pragma unroll
+        for (int m = 0; m < E; ++m) {
+            const int jx = t + m * TL;
+            const int jm = (jx == 0) ? 0 : nx - jx;
+            const C h1 = v[m];
+            const C h2 = sx[jm * W + partner];
+            const int kx = kvec_dev(jx, nx);
+            const int k2a = kx * kx + kys * kys;
+            const int k2b = k2a + M * M;
+            const T d0 = (k2a == 0) ? (T)0 : a.coef / (T)k2a;
+            const T d1 = a.coef / (T)k2b;
+            const T sp = (d0 + d1) * (T)0.5, sm = (d0 - d1) * (T)0.5;
+            v[m] = C{sp * h1.x + sm * h2.x, sp * h1.y - sm * h2.y};
+        }
+    }
+    __syncthreads();
+    line_fft<true>(v, t, a.pl, stw, sx, map, active);
+    if (active && !(side == 1 && row == ky)) {
+#pragma unroll
+        for (int m = 0; m < E; ++m) base[m * step] = v[m];
+    }
+}
+
+} // namespace psolve

@@ -1,0 +1,48 @@
+// z-direction passes: real rows <-> packed half-spectrum rows.
+#include "launch.h"
+
+namespace psolve {
+
+template <typename T, int E, typename K>
+static cudaError_t run(K kernel, const ZArgs<T> &a, unsigned grid, unsigned block, size_t smem,
+                       cudaStream_t s)
+{
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    kernel<<<grid, block, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+#define PSOLVE_Z_DISPATCH(KERNEL)                                                   \
+    switch (a.pl.E) {                                                               \
+    case 2: return run<T, 2>(KERNEL<T, 2>, a, grid, block, smem, s);                \
+    case 3: return run<T, 3>(KERNEL<T, 3>, a, grid, block, smem, s);                \
+    case 4: return run<T, 4>(KERNEL<T, 4>, a, grid, block, smem, s);                \
+    case 6: return run<T, 6>(KERNEL<T, 6>, a, grid, block, smem, s);                \
+    case 8: return run<T, 8>(KERNEL<T, 8>, a, grid, block, smem, s);                \
+    case 12: return run<T, 12>(KERNEL<T, 12>, a, grid, block, smem, s);             \
+    case 16: return run<T, 16>(KERNEL<T, 16>, a, grid, block, smem, s);             \
+    case 24: return run<T, 24>(KERNEL<T, 24>, a, grid, block, smem, s);             \
+    default: return cudaErrorInvalidValue;                                          \
+    }
+
+template <typename T>
+cudaError_t launch_zfwd(const ZArgs<T> &a, unsigned grid, unsigned block, size_t smem, cudaStream_t s)
+{
+    PSOLVE_Z_DISPATCH(k_zfwd)
+}
+
+template <typename T>
+cudaError_t launch_zinv(const ZArgs<T> &a, unsigned grid, unsigned block, size_t smem, cudaStream_t s)
+{
+    PSOLVE_Z_DISPATCH(k_zinv)
+}
+
+template cudaError_t launch_zfwd<float>(const ZArgs<float> &, unsigned, unsigned, size_t, cudaStream_t);
+template cudaError_t launch_zfwd<double>(const ZArgs<double> &, unsigned, unsigned, size_t, cudaStream_t);
+template cudaError_t launch_zinv<float>(const ZArgs<float> &, unsigned, unsigned, size_t, cudaStream_t);
+template cudaError_t launch_zinv<double>(const ZArgs<double> &, unsigned, unsigned, size_t, cudaStream_t);
+
+} // namespace psolve

@@ -1,0 +1,77 @@
+"""The C ABI library builds, loads and exports every declared symbol; the
+host-side argument checks answer without a GPU (CPU only)."""
+import ctypes
+import os
+import re
+
+import pytest
+import torch
+
+from paper_1408_6497_gb300 import _lib, build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "psolve.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return _lib.load()
+
+
+def declared_symbols():
+    text = open(HEADER).read()
+    return sorted(set(re.findall(r"\b(psolve_[a-z_]+)\s*\(", text)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_symbols()
+    assert len(names) >= 14
+    for name in names:
+        assert hasattr(lib, name), name
+    assert set(names) == set(_lib.EXPORTS)
+
+
+def test_version_and_status_strings(lib):
+    assert lib.psolve_version() == 100
+    assert lib.psolve_status_string(0) == b"ok"
+    assert lib.psolve_status_string(2) == b"unsupported size"
+
+
+@pytest.mark.parametrize("dims", [(5, 8, 8), (8, 7, 8), (8, 8, 10), (2, 8, 8), (4096, 4, 4),
+                                  (8, 8, 14), (9, 8, 8), (0, 8, 8), (-4, 8, 8)])
+def test_unsupported_sizes_rejected_before_any_cuda_call(lib, dims):
+    h = ctypes.c_void_p(123)
+    rc = lib.psolve_plan_create(*dims, _lib.F32, 1, ctypes.byref(h))
+    assert rc == 2
+    assert h.value is None
+    assert b"2^a 3^b" in lib.psolve_last_error()
+
+
+def test_bad_arguments_rejected(lib):
+    h = ctypes.c_void_p()
+    assert lib.psolve_plan_create(8, 8, 8, _lib.F32, 0, ctypes.byref(h)) == 1
+    assert lib.psolve_plan_create(8, 8, 8, 9, 1, ctypes.byref(h)) == 1
+    assert lib.psolve_plan_create(8, 8, 8, _lib.F32, 1, None) == 1
+    assert lib.psolve_execute(None, None, None, None) == 1
+    assert lib.psolve_adjoint(None, None, None, None) == 1
+    assert lib.psolve_destroy(None) == 1
+    assert lib.psolve_instance_offset(None, 0) == ctypes.c_size_t(-1).value
+    assert lib.psolve_total_elements(None) == 0
+    arr = (ctypes.c_int * 2)(8, 7)
+    ok = (ctypes.c_int * 2)(8, 8)
+    assert lib.psolve_plan_create_many(ok, arr, ok, 2, _lib.F32, ctypes.byref(h)) == 2
+    assert b"instance 1" in lib.psolve_last_error()
+
+
+@pytest.mark.skipif(torch.cuda.is_available(), reason="checks the no-device path")
+def test_valid_plan_without_device_fails_loudly(lib):
+    h = ctypes.c_void_p()
+    rc = lib.psolve_plan_create(8, 8, 8, _lib.F32, 1, ctypes.byref(h))
+    assert rc == 4  # PSOLVE_ERR_CUDA, not a silent CPU path
+    assert h.value is None
+
+
+def test_binding_raises_when_library_missing(tmp_path):
+    with pytest.raises(RuntimeError, match="no CPU fallback"):
+        _lib.load(str(tmp_path / "libpsolve.so"))

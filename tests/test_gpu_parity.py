@@ -1,0 +1,208 @@
+"""CUDA path vs the FP64 oracle, element by element, through the C ABI.
+
+Tolerances (relative L2 against the oracle solving the same rounded input):
+FP64 1e-12, FP32 5e-6.  Wavenumber indexing is compared bit-exactly.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from oracle import closed_form as cf
+from paper_1408_6497_gb300 import Plan, error_norms, poisson_solve
+from paper_1408_6497_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"f64": 1e-12, "f32": 5e-6}
+NP = {"f64": np.float64, "f32": np.float32}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _setup():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1408_6497_gb300 import build
+    build.build()
+    oracle.build()
+
+
+def gpu_solve(f64, prec, batch=1):
+    f = f64.astype(NP[prec])
+    plan = Plan(f.shape[-3:], dtype=prec, batch=batch)
+    ft = torch.from_numpy(np.ascontiguousarray(f).ravel()).cuda()
+    u = plan.execute(ft)
+    plan.status()
+    return u.cpu().numpy().reshape(f.shape), f
+
+
+SHAPES = [(4, 4, 4), (8, 6, 4), (6, 6, 6), (12, 24, 48), (16, 32, 64), (24, 32, 48), (96, 48, 24),
+          (18, 54, 12), (4, 6, 8), (64, 64, 64), (128, 96, 24), (36, 12, 6), (48, 16, 256),
+          (2048, 4, 8), (4, 2048, 4), (8, 4, 2048), (162, 8, 18), (32, 32, 1024)]
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("shape", SHAPES)
+def test_random_field_parity(prec, shape):
+    f64 = wl.random_field(shape, seed=100 + sum(shape))
+    u, f_in = gpu_solve(f64, prec)
+    ref = oracle.solve(f_in.astype(np.float64))
+    err = oracle.rel_l2(u, ref)
+    assert err <= TOL[prec], (shape, prec, err)
+
+
+def test_config1_fp64_mode_sum_closed_form():
+    w = wl.mode_sum()
+    u, _ = gpu_solve(w.f, "f64")
+    ref = oracle.solve(w.f)
+    exact = cf.mode_sum_u(w.modes.k, w.modes.a, w.modes.phi, w.shape)
+    assert oracle.rel_l2(u, ref) <= 1e-12
+    assert oracle.rel_l2(u, exact) <= 1e-12
+
+
+def test_config2_fp32_gaussians_256():
+    w = wl.gaussians16()
+    u, f_in = gpu_solve(w.f, "f32")
+    ref = oracle.solve(f_in.astype(np.float64))
+    err = oracle.rel_l2(u, ref)
+    print(f"256^3 gaussians FP32 rel-L2 {err:.3e} rel-linf {oracle.rel_linf(u, ref):.3e}")
+    assert err <= 5e-6
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("shape", [(8, 8, 8), (12, 6, 16)])
+def test_single_modes_and_nyquist(prec, shape):
+    nx, ny, nz = shape
+    x = np.arange(nx)[:, None, None] / nx
+    y = np.arange(ny)[None, :, None] / ny
+    z = np.arange(nz)[None, None, :] / nz
+    ks = [(1, 2, 1), (-1, 2, -1), (1, -2, -1), (nx // 2, 0, 0), (0, ny // 2, 0), (0, 0, nz // 2),
+          (nx // 2, ny // 2, nz // 2), (1, ny // 2, nz // 2), (0, 0, 1), (2, 0, nz // 2)]
+    for k in ks:
+        for trig in (np.cos, np.sin):
+            f = trig(2 * np.pi * (k[0] * x + k[1] * y + k[2] * z))
+            if np.abs(f).max() < 0.5:
+                continue
+            u, _ = gpu_solve(f, prec)
+            exact = f / (4 * np.pi ** 2 * (k[0] ** 2 + k[1] ** 2 + k[2] ** 2))
+            assert np.abs(u - exact).max() <= 10 * TOL[prec] * np.abs(exact).max(), (k, trig)
+
+
+@pytest.mark.parametrize("shape", [(8, 8, 8), (24, 12, 48), (6, 10, 4)])
+def test_kvec_bit_exact(shape):
+    plan = Plan(shape, dtype="f32")
+    k = plan.debug_kvec(0)
+    nx, ny, nz = shape
+    kx, ky, kz = oracle.kvec(nx), oracle.kvec(ny), oracle.kvec(nz)
+    H = nz // 2 + 1
+    np.testing.assert_array_equal(k[..., 0], np.broadcast_to(kx[:, None, None], (nx, ny, H)))
+    np.testing.assert_array_equal(k[..., 1], np.broadcast_to(ky[None, :, None], (nx, ny, H)))
+    np.testing.assert_array_equal(k[..., 2], np.broadcast_to(kz[None, None, :H], (nx, ny, H)))
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_in_place(prec):
+    shape = (16, 24, 12)
+    f64 = wl.random_field(shape, seed=7)
+    plan = Plan(shape, dtype=prec)
+    ft = torch.from_numpy(f64.astype(NP[prec]).ravel()).cuda()
+    ref = plan.execute(ft.clone())
+    plan.execute(ft, ft)
+    assert torch.equal(ft, ref)
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_uniform_batch(prec):
+    shape, B = (12, 16, 24), 3
+    fs = [wl.random_field(shape, seed=40 + b) for b in range(B)]
+    f = np.stack(fs)
+    u, f_in = gpu_solve(f, prec, batch=B)
+    for b in range(B):
+        assert oracle.rel_l2(u[b], oracle.solve(f_in[b].astype(np.float64))) <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_uneven_batch(prec):
+    shapes = wl.batch_shapes(8)
+    plan = Plan(dtype=prec, shapes=shapes)
+    flat = plan.empty()
+    fs = []
+    for b, s in enumerate(shapes):
+        w = wl.batch_instance(s, b)
+        fs.append(w.f.astype(NP[prec]))
+        plan.view(flat, b).copy_(torch.from_numpy(fs[-1]))
+    u = plan.execute(flat)
+    for b, s in enumerate(shapes):
+        ref = oracle.solve(fs[b].astype(np.float64))
+        assert oracle.rel_l2(plan.view(u, b).cpu().numpy(), ref) <= TOL[prec], s
+
+
+def test_execute_host_matches_device():
+    shape = (32, 16, 48)
+    f = wl.random_field(shape, seed=12).astype(np.float32)
+    plan = Plan(shape, dtype="f32")
+    u_dev = plan.execute(torch.from_numpy(f.ravel()).cuda()).cpu().numpy()
+    u_host = plan.execute_host(f.ravel())
+    np.testing.assert_array_equal(u_dev, u_host)
+
+
+def test_adjoint_symmetry_and_autograd_fp64():
+    shape = (16, 12, 8)
+    x = torch.from_numpy(wl.random_field(shape, seed=1)).cuda()
+    y = torch.from_numpy(wl.random_field(shape, seed=2)).cuda()
+    plan = Plan(shape, dtype="f64")
+    ax = plan.execute(x.ravel())
+    ay = plan.adjoint(y.ravel())
+    lhs = float((ax * y.ravel()).sum())
+    rhs = float((x.ravel() * ay).sum())
+    assert abs(lhs - rhs) <= 1e-13 * abs(lhs)
+
+
+def test_gradient_64_fp64_vs_oracle_and_fd():
+    shape = (64, 64, 64)
+    f64 = wl.sharp_source(shape).f
+    ut = wl.smooth_target(shape).f * 1e-3
+    f = torch.from_numpy(f64).cuda().requires_grad_(True)
+    target = torch.from_numpy(ut).cuda()
+    u = poisson_solve(f)
+    loss = 0.5 * ((u - target) ** 2).sum()
+    loss.backward()
+    g_or = oracle.gradient(f64, ut)
+    assert oracle.rel_l2(f.grad.cpu().numpy(), g_or) <= 1e-12
+
+    def L(v):
+        with torch.no_grad():
+            r = poisson_solve(v) - target
+            return 0.5 * float((r * r).sum())
+
+    rng = np.random.default_rng(3)
+    h = 1e-4
+    for _ in range(3):
+        d = torch.from_numpy(rng.standard_normal(shape)).cuda()
+        fd = (L(f.detach() + h * d) - L(f.detach() - h * d)) / (2 * h)
+        an = float((f.grad * d).sum())
+        assert abs(fd - an) <= 1e-6 * abs(an)
+
+
+def test_error_norms_kernel():
+    a = torch.randn(1000, dtype=torch.float64, device="cuda")
+    b = a + 1e-3 * torch.randn(1000, dtype=torch.float64, device="cuda")
+    l2, linf = error_norms(b, a)
+    an, bn = a.cpu().numpy(), b.cpu().numpy()
+    assert l2 == pytest.approx(oracle.rel_l2(bn, an), rel=1e-12)
+    assert linf == pytest.approx(oracle.rel_linf(bn, an), rel=1e-12)
+
+
+def test_argument_errors_on_device():
+    from paper_1408_6497_gb300 import _lib
+    plan = Plan((8, 8, 8), dtype="f32")
+    buf = torch.zeros(2 * 512 + 8, dtype=torch.float32, device="cuda")
+    lib = _lib.load()
+    base = buf.data_ptr()
+    # misaligned pointer
+    assert lib.psolve_execute(plan.handle, base + 4, base + 4096, None) == 1
+    # partial overlap of f and u
+    assert lib.psolve_execute(plan.handle, base, base + 64, None) == 1
+    # exact aliasing is allowed
+    assert lib.psolve_execute(plan.handle, base, base, None) == 0
+    torch.cuda.synchronize()
