@@ -88,7 +88,7 @@ def test_single_modes_and_nyquist(prec, shape):
             assert np.abs(u - exact).max() <= 10 * TOL[prec] * np.abs(exact).max(), (k, trig)
 
 
-@pytest.mark.parametrize("shape", [(8, 8, 8), (24, 12, 48), (6, 10, 4)])
+@pytest.mark.parametrize("shape", [(8, 8, 8), (24, 12, 48), (6, 12, 4)])
 def test_kvec_bit_exact(shape):
     plan = Plan(shape, dtype="f32")
     k = plan.debug_kvec(0)
