@@ -131,6 +131,30 @@ const char *psolve_pass_name(const psolve_plan *plan, int i);
 /* Number of kernel launches one psolve_execute enqueues; 0 on error. */
 int psolve_launches_per_solve(const psolve_plan *plan);
 
+/* Allocation-free solve, for callers that cannot allocate device memory:
+ * code inside a custom allocator or memory-pool callback, frameworks that
+ * forbid allocation during a step, hosts that reserve all device memory up
+ * front.  The paper has no counterpart; it is psolve_execute for one grid
+ * nx × ny × nz (same checks, same kernels, same result) without a plan.
+ * It calls no cudaMalloc, cudaFree or other allocating routine.  The only
+ * memory besides f and u is the twiddle tables, held in one fixed 64 KiB
+ * device array inside the library (every GPU that loads the library keeps
+ * it until the process exits); a grid needs (nx + ny + nz) complex values
+ * there (8 B each in FP32, 16 B in FP64), so every valid FP32 grid fits and
+ * an FP64 grid fits while nx + ny + nz <= 4096; larger grids return
+ * PSOLVE_ERR_UNSUPPORTED_SIZE before anything is enqueued.
+ * dtype: PSOLVE_F32 or PSOLVE_F64 (else PSOLVE_ERR_INVALID_ARG).  f, u:
+ * device pointers as for psolve_execute (u == f allowed).
+ * The first call on each device looks up the array's device address with
+ * that device current (cudaGetSymbolAddress); make it before any stream
+ * capture.  Every call rewrites the whole array on `stream` before its
+ * kernels read it, so nothing carries over from the previous call, but calls
+ * whose work overlaps on the GPU (different streams, no ordering) race on
+ * the shared array and give wrong results: order them.
+ * psolve_last_error() is not updated by this call. */
+psolve_status psolve_execute_noalloc(int nx, int ny, int nz, int dtype, const void *f, void *u,
+                                     void *stream);
+
 /* Static description of a status code. */
 const char *psolve_status_string(psolve_status s);
 

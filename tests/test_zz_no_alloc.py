@@ -1,0 +1,84 @@
+"""psolve_execute_noalloc, the allocation-free solve, through the C ABI.
+
+Callers that cannot allocate device memory (code inside an allocator or
+memory-pool callback, frameworks that forbid allocation during a step, hosts
+that reserve all device memory up front) use this entry point: it keeps its
+twiddle tables in a fixed 64 KiB array inside the library instead of a plan.
+Its result must match psolve_execute's, call after call, even though every
+call reuses the same shared array.  This file is collected last on purpose.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+from paper_1408_6497_gb300 import Plan, _lib
+from paper_1408_6497_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"f64": 1e-12, "f32": 5e-6}
+NP = {"f64": np.float64, "f32": np.float32}
+CODE = {"f64": _lib.F64, "f32": _lib.F32}
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1408_6497_gb300 import build
+    build.build()
+    return _lib.load()
+
+
+def rel_l2(a, b):
+    a = a.double()
+    b = b.double()
+    return float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b))
+
+
+def noalloc_solve(lib, prec, shape, f):
+    u = torch.empty_like(f)
+    stream = torch.cuda.current_stream().cuda_stream
+    rc = lib.psolve_execute_noalloc(*shape, CODE[prec], f.data_ptr(), u.data_ptr(), stream)
+    assert rc == 0, _lib.STATUS.get(rc, rc)
+    torch.cuda.synchronize()
+    return u
+
+
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_noalloc_matches_planned_solve_on_consecutive_calls(lib, prec):
+    # Two different grids, then the first again: the shared table array is
+    # rewritten by each call, so no call may see the previous call's tables.
+    shapes = [(48, 32, 96), (24, 64, 18), (48, 32, 96)]
+    for i, shape in enumerate(shapes):
+        f = torch.from_numpy(wl.random_field(shape, seed=900 + i).astype(NP[prec]).ravel()).cuda()
+        ref = Plan(shape, dtype=prec).execute(f)
+        u = noalloc_solve(lib, prec, shape, f)
+        err = rel_l2(u, ref)
+        assert err <= TOL[prec], (shape, prec, err)
+
+
+def test_noalloc_in_place_and_twice_in_a_row(lib):
+    shape = (32, 32, 32)
+    f = torch.from_numpy(wl.mode_sum(shape).f.astype(np.float32).ravel()).cuda()
+    ref = Plan(shape, dtype="f32").execute(f)
+    stream = torch.cuda.current_stream().cuda_stream
+    for _ in range(2):
+        g = f.clone()
+        rc = lib.psolve_execute_noalloc(*shape, _lib.F32, g.data_ptr(), g.data_ptr(), stream)
+        assert rc == 0
+        torch.cuda.synchronize()
+        assert rel_l2(g, ref) <= TOL["f32"]
+
+
+def test_noalloc_rejects_grids_beyond_the_table_array(lib):
+    # FP64 tables for nx + ny + nz = 4100 need 65600 bytes > 64 KiB: refused
+    # on the host before anything is enqueued (the pointers are never used).
+    fake = ctypes.c_void_p(1 << 20)
+    rc = lib.psolve_execute_noalloc(2048, 2048, 4, _lib.F64, fake, fake, None)
+    assert rc == 2
+    # the same grid in FP32 fits, as do sizes outside the solver's range: checked first
+    assert lib.psolve_execute_noalloc(10, 8, 8, _lib.F32, fake, fake, None) == 2
+    assert lib.psolve_execute_noalloc(8, 8, 8, _lib.F32_TC, fake, fake, None) == 1
