@@ -4,9 +4,13 @@
 #include "psolve.h"
 #include "launch.h"
 
+#include <cudaTypedefs.h>
+
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <memory>
@@ -93,19 +97,75 @@ bool make_line_plan(int L, LinePlan &p)
 }
 
 size_t csize(int dtype) { return dtype == PSOLVE_F64 ? 16 : 8; }
+
+} // namespace
+
+// Stage plan with a given number of points per thread E (a power of two
+// dividing L): the largest power-of-two radices (<= 16) dividing E.
+bool make_line_plan_E(int L, int E, LinePlan &p)
+{
+    int a, b;
+    if (!factor23(L, a, b) || b != 0 || L % E != 0 || !supported_E(E)) return false;
+    std::memset(&p, 0, sizeof(p));
+    p.L = L;
+    p.E = E;
+    p.TL = L / E;
+    int p2 = 1;
+    while (E % (p2 * 2) == 0 && p2 * 2 <= 16) p2 *= 2;
+    std::vector<int> rad;
+    int rem = L;
+    while (rem > 1) {
+        const int r = std::min(p2, rem);
+        rad.push_back(r);
+        rem /= r;
+    }
+    if ((int)rad.size() > kMaxStages) return false;
+    p.nst = (int)rad.size();
+    int ns = 1;
+    for (int s = 0; s < p.nst; ++s) {
+        p.radix[s] = rad[s];
+        p.ns[s] = ns;
+        p.twstep[s] = L / (ns * rad[s]);
+        ns *= rad[s];
+    }
+    return true;
+}
+
+namespace {
 size_t rsize(int dtype) { return dtype == PSOLVE_F64 ? 8 : 4; }
 
 int zpitch(int M) { return M + (M >> 4) + 1; }
 size_t z_smem(const Group &g, int dtype) { return (size_t)(g.M + (size_t)g.Wz * zpitch(g.M)) * csize(dtype); }
 size_t s_smem(int L, int W, int dtype) { return (size_t)L * (1 + W) * csize(dtype); }
 
+// Optional override "Wz,Wy,Wx" from PSOLVE_TILE_W (tuning runs); a value
+// that breaks a launch limit is ignored.
+void override_tiles(Group &g, int dtype)
+{
+    const char *env = std::getenv("PSOLVE_TILE_W");
+    if (!env) return;
+    int wz = 0, wy = 0, wx = 0;
+    if (std::sscanf(env, "%d,%d,%d", &wz, &wy, &wx) != 3) return;
+    const bool fp64 = dtype == PSOLVE_F64;
+    if (wz >= 1 && wz * g.pz.TL <= max_threads(fp64, g.pz.E)) {
+        const int keep = g.Wz;
+        g.Wz = wz;
+        if (z_smem(g, dtype) > kSmemCap) g.Wz = keep;
+    }
+    if (wy >= 1 && wy <= g.M && wy * g.py.TL <= max_threads(fp64, g.py.E) &&
+        s_smem(g.ny, wy, dtype) <= kSmemCap)
+        g.Wy = wy;
+    if (wx >= 2 && wx * g.px.TL <= max_threads(fp64, g.px.E) && s_smem(g.nx, wx, dtype) <= kSmemCap)
+        g.Wx = wx;
+}
+
 void choose_tiles(Group &g, int dtype)
 {
     const bool fp64 = dtype == PSOLVE_F64;
-    // z: about 256 threads, W rows each of TL threads.
+    // z: about 128 threads, W rows each of TL threads (8 rows of 256 points).
     {
         const int mt = max_threads(fp64, g.pz.E);
-        g.Wz = std::max(1, std::min(256, mt) / g.pz.TL);
+        g.Wz = std::max(1, std::min(128, mt) / g.pz.TL);
         while (g.Wz > 1 && z_smem(g, dtype) > kSmemCap) g.Wz /= 2;
     }
     // y and x: W adjacent columns (16 columns = 128 B runs in FP32).
@@ -123,6 +183,7 @@ void choose_tiles(Group &g, int dtype)
         while (W > 2 && s_smem(g.nx, W, dtype) > kSmemCap) W /= 2;
         g.Wx = W;
     }
+    override_tiles(g, dtype);
 }
 
 } // namespace
@@ -131,6 +192,9 @@ struct psolve_plan {
     unsigned magic;
     int dtype;
     int device;
+    int num_sms;
+    bool use_tma;
+    int tma_narrow_y, tma_narrow_x; // tile variant per pass (see launch.h)
     int batch;
     std::vector<Group> groups;
     std::vector<size_t> inst_off;
@@ -263,6 +327,22 @@ psolve_status build_plan(const std::vector<int> &nx, const std::vector<int> &ny,
 
     cudaError_t e = cudaGetDevice(&p->device);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    e = cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute");
+    {
+        const char *env = std::getenv("PSOLVE_TMA");
+        p->use_tma = !(env && env[0] == '0');
+        // "y,x" tile variants of the TMA passes (0 wide, 1 narrow); narrow
+        // tiles only while their rows stay >= 64 bytes (W >= 8 columns).
+        p->tma_narrow_y = -1;
+        p->tma_narrow_x = -1;
+        const char *nv = std::getenv("PSOLVE_TMA_NARROW");
+        int ny_ = 0, nx_ = 0;
+        if (nv && std::sscanf(nv, "%d,%d", &ny_, &nx_) == 2) {
+            p->tma_narrow_y = ny_ < 0 || ny_ > 2 ? 0 : ny_;
+            p->tma_narrow_x = nx_ < 0 || nx_ > 2 ? 0 : nx_;
+        }
+    }
     e = cudaMalloc(&p->tables, tcount * csize(dtype));
     if (e != cudaSuccess) {
         p->tables = nullptr;
@@ -295,6 +375,84 @@ psolve_status build_plan(const std::vector<int> &nx, const std::vector<int> &ny,
 }
 
 unsigned ceil_div(long long a, long long b) { return (unsigned)((a + b - 1) / b); }
+
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    return fn;
+}
+
+// 3D map over complex FP32 values seen as 8-byte elements, dims innermost first.
+bool encode_map(CUtensorMap *m, void *base, uint64_t d0, uint64_t d1, uint64_t d2, uint32_t b0, uint32_t b1,
+                uint32_t b2)
+{
+    auto fn = tensor_map_encoder();
+    if (!fn) return false;
+    cuuint64_t dims[3] = {d0, d1, d2};
+    cuuint64_t strides[2] = {d0 * 8, d0 * d1 * 8};
+    cuuint32_t box[3] = {b0, b1, b2};
+    cuuint32_t es[3] = {1, 1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_INT64, 3, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// Whether the persistent TMA pass applies to lines of length L over M columns.
+int tma_variant(int setting, int L) { return setting >= 0 ? setting : (tma_columns(L, 1) >= 8 ? 1 : 0); }
+
+bool tma_fits(const psolve_plan *p, int L, int M, int narrow)
+{
+    return p->use_tma && p->dtype != PSOLVE_F64 && tma_supported(L) && (M % 2) == 0 &&
+           M >= tma_columns(L, narrow);
+}
+
+template <typename T>
+psolve_status run_tma_pass(const psolve_plan *p, const Group &g, T *ui, int kind, cudaStream_t s)
+{
+    if constexpr (sizeof(T) != 4) {
+        return fail(PSOLVE_ERR_INTERNAL, "TMA pass is FP32 only");
+    } else {
+        const int L = kind == 2 ? g.nx : g.ny;
+        const int narrow = tma_variant(kind == 2 ? p->tma_narrow_x : p->tma_narrow_y, L);
+        const int W = tma_columns(L, narrow);
+        const int boxr = L < 256 ? L : 256;
+        CUtensorMap map;
+        const bool ok = kind == 2
+                            ? encode_map(&map, ui, (uint64_t)g.M, (uint64_t)g.ny, (uint64_t)g.nx * g.count,
+                                         (uint32_t)W, 1u, (uint32_t)boxr)
+                            : encode_map(&map, ui, (uint64_t)g.M, (uint64_t)g.ny, (uint64_t)g.nx * g.count,
+                                         (uint32_t)W, (uint32_t)boxr, 1u);
+        if (!ok) return fail(PSOLVE_ERR_CUDA, "cuTensorMapEncodeTiled failed");
+        TmaArgs a{};
+        a.data = reinterpret_cast<float2 *>(ui);
+        a.M = g.M;
+        a.ny = g.ny;
+        a.ncb = (g.M + W - 1) / W;
+        a.main_tiles = kind == 2 ? (long long)g.count * g.ny * a.ncb : (long long)g.count * g.nx * a.ncb;
+        a.sInst = (long long)g.nx * g.ny * g.M;
+        a.npairs = (long long)g.count * (g.ny / 2 + 1);
+        a.tw = reinterpret_cast<const float2 *>(p->tables) + (kind == 2 ? g.tw_x : g.tw_y);
+        a.coef = (float)(1.0 / (4.0 * M_PI * M_PI * ((double)g.nx * g.ny * g.nz)));
+        a.status = p->status;
+        if (narrow == 2 && kind == 2 && !make_line_plan_E(g.nx, 8, a.pl_x))
+            return fail(PSOLVE_ERR_INTERNAL, "no 8-point plan for the x line");
+        long long work = a.main_tiles;
+        if (kind == 2) work = std::max(work, (a.npairs + W / 2 - 1) / (W / 2));
+        const unsigned grid = (unsigned)std::min<long long>(work, (long long)p->num_sms * (narrow ? 2 : 1));
+        cudaError_t e = launch_strided_tma(map, a, L, kind, narrow, grid, s);
+        if (e != cudaSuccess) return cuda_fail(e, "TMA pass");
+        return PSOLVE_OK;
+    }
+}
 
 template <typename T>
 psolve_status run_group(const psolve_plan *p, const Group &g, const T *f, T *u, cudaStream_t s,
@@ -340,8 +498,15 @@ psolve_status run_group(const psolve_plan *p, const Group &g, const T *f, T *u, 
     const unsigned ygrid = (unsigned)(y.nplanes * y.ncb);
     const unsigned yblock = (unsigned)(g.Wy * g.py.TL);
     const size_t ysm = s_smem(g.ny, g.Wy, dtype);
-    e = launch_ypass<T>(y, false, ygrid, yblock, ysm, s);
-    if (e != cudaSuccess) return cuda_fail(e, "y forward pass");
+    const bool tma_y = tma_fits(p, g.ny, g.M, tma_variant(p->tma_narrow_y, g.ny));
+    const bool tma_x = tma_fits(p, g.nx, g.M, tma_variant(p->tma_narrow_x, g.nx));
+    if (tma_y) {
+        psolve_status st = run_tma_pass<T>(p, g, ui, 0, s);
+        if (st != PSOLVE_OK) return st;
+    } else {
+        e = launch_ypass<T>(y, false, ygrid, yblock, ysm, s);
+        if (e != cudaSuccess) return cuda_fail(e, "y forward pass");
+    }
     mark(2);
 
     XArgs<T> x{};
@@ -361,12 +526,22 @@ psolve_status run_group(const psolve_plan *p, const Group &g, const T *f, T *u, 
     x.coef = (T)(1.0 / (4.0 * M_PI * M_PI * N));
     const unsigned xgrid = (unsigned)(x.main_tiles + (x.npairs + g.Wx / 2 - 1) / (g.Wx / 2));
     const unsigned xblock = (unsigned)(g.Wx * g.px.TL);
-    e = launch_xfused<T>(x, xgrid, xblock, s_smem(g.nx, g.Wx, dtype), s);
-    if (e != cudaSuccess) return cuda_fail(e, "x pass with spectral division");
+    if (tma_x) {
+        psolve_status st = run_tma_pass<T>(p, g, ui, 2, s);
+        if (st != PSOLVE_OK) return st;
+    } else {
+        e = launch_xfused<T>(x, xgrid, xblock, s_smem(g.nx, g.Wx, dtype), s);
+        if (e != cudaSuccess) return cuda_fail(e, "x pass with spectral division");
+    }
     mark(3);
 
-    e = launch_ypass<T>(y, true, ygrid, yblock, ysm, s);
-    if (e != cudaSuccess) return cuda_fail(e, "y inverse pass");
+    if (tma_y) {
+        psolve_status st = run_tma_pass<T>(p, g, ui, 1, s);
+        if (st != PSOLVE_OK) return st;
+    } else {
+        e = launch_ypass<T>(y, true, ygrid, yblock, ysm, s);
+        if (e != cudaSuccess) return cuda_fail(e, "y inverse pass");
+    }
     mark(4);
 
     ZArgs<T> zi = z;

@@ -34,6 +34,13 @@ template <typename C> __device__ __forceinline__ C cmulc(C a, C b)
     return {a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y};
 }
 template <typename C, typename S> __device__ __forceinline__ C cscale(C a, S s) { return {a.x * s, a.y * s}; }
+
+#if defined(__CUDA_ARCH__) && (__CUDA_ARCH__ >= 1000) && defined(PSOLVE_F32X2)
+// Blackwell packed FP32x2 arithmetic: one instruction per complex add/sub
+// (opt-in: measured slower than scalar FADDs on the z passes).
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
+#endif
 template <typename C> __device__ __forceinline__ C cconj(C a) { return {a.x, -a.y}; }
 
 // Multiply by -i (forward direction) or +i (inverse direction).
@@ -109,11 +116,17 @@ template <bool INV, typename C> __device__ __forceinline__ void dft3(C *a)
 template <bool INV, typename C> __device__ __forceinline__ void dft4(C *a)
 {
     C a0 = cadd(a[0], a[2]), a1 = csub(a[0], a[2]);
-    C a2 = cadd(a[1], a[3]), a3 = rot90<INV>(csub(a[1], a[3]));
+    C a2 = cadd(a[1], a[3]), d = csub(a[1], a[3]);
     a[0] = cadd(a0, a2);
     a[2] = csub(a0, a2);
-    a[1] = cadd(a1, a3);
-    a[3] = csub(a1, a3);
+    // a1 ∓ i·d (forward: out1 = a1 - i d, out3 = a1 + i d)
+    if (INV) {
+        a[1] = C{a1.x - d.y, a1.y + d.x};
+        a[3] = C{a1.x + d.y, a1.y - d.x};
+    } else {
+        a[1] = C{a1.x + d.y, a1.y - d.x};
+        a[3] = C{a1.x - d.y, a1.y + d.x};
+    }
 }
 
 template <bool INV, typename C> __device__ __forceinline__ void dft8(C *a)
@@ -282,6 +295,150 @@ __device__ __forceinline__ void line_fft(C (&v)[E], int t, const LinePlan &pl,
             }
             __syncthreads();
         }
+    }
+}
+
+// ------------------------------------------------- compile-time line plans
+// The same stage plan as the host's make_line_plan, evaluated at compile time
+// for hot line lengths: radix-3 stages first, then the largest power-of-two
+// radices (<= 16) dividing E.  With every stage constant, the j mod Ns and
+// twiddle-index arithmetic folds to shifts and masks.
+constexpr int ct_pow2(int L) { int a = 0; while (L % 2 == 0) { L /= 2; ++a; } return a; }
+constexpr int ct_pow3(int L)
+{
+    while (L % 2 == 0) L /= 2;
+    int b = 0;
+    while (L % 3 == 0) { L /= 3; ++b; }
+    return b;
+}
+constexpr int ct_min(int a, int b) { return a < b ? a : b; }
+constexpr int ct_E(int L)
+{
+    return ct_pow3(L) > 0 ? 3 * (1 << ct_min(ct_pow2(L), 3)) : (1 << ct_min(ct_pow2(L), 4));
+}
+constexpr int ct_p2(int E) { int p = 1; while (E % (p * 2) == 0 && p * 2 <= 16) p *= 2; return p; }
+constexpr int ct_radix(int L, int s, int E = 0)
+{
+    const int b = ct_pow3(L);
+    if (s < b) return 3;
+    int rem = 1 << ct_pow2(L);
+    const int p2 = ct_p2(E > 0 ? E : ct_E(L));
+    for (int i = b;; ++i) {
+        const int r = p2 < rem ? p2 : rem;
+        if (i == s) return rem > 1 ? r : 1;
+        rem /= r;
+    }
+}
+constexpr int ct_nst(int L, int E = 0)
+{
+    int n = 0;
+    while (ct_radix(L, n, E) > 1) ++n;
+    return n;
+}
+constexpr int ct_ns(int L, int s, int E = 0)
+{
+    int ns = 1;
+    for (int i = 0; i < s; ++i) ns *= ct_radix(L, i, E);
+    return ns;
+}
+
+template <int R, bool INV, bool LAST, int TL, int NS, int TWS, int E, typename C, typename Map>
+__device__ __forceinline__ void fft_stage_ct(C (&v)[E], int t, const C *__restrict__ tw, C *sm,
+                                             const Map &map, bool active)
+{
+    constexpr int NB = E / R;
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+        const int j = t + b * TL;
+        const int jm = j % NS;
+        C a[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) a[r] = v[b + r * NB];
+        if constexpr (NS > 1) {
+            const int q = jm * TWS;
+#pragma unroll
+            for (int r = 1; r < R; ++r) {
+                const C w = tw[r * q];
+                a[r] = INV ? cmulc(a[r], w) : cmul(a[r], w);
+            }
+        }
+        dft<R, INV>(a);
+        if constexpr (LAST) {
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[b + r * NB] = a[r];
+        } else {
+            if (active) {
+                const int base = (j - jm) * R + jm;
+#pragma unroll
+                for (int r = 0; r < R; ++r) sm[map(base + r * NS)] = a[r];
+            }
+        }
+    }
+}
+
+template <bool INV, int L, int S, int E, typename C, typename Map>
+__device__ __forceinline__ void line_fft_ct_from(C (&v)[E], int t, const C *__restrict__ tw, C *sm,
+                                                 const Map &map, bool active)
+{
+    constexpr int NST = ct_nst(L, E);
+    if constexpr (S < NST) {
+        constexpr int R = ct_radix(L, S, E);
+        constexpr int NS = ct_ns(L, S, E);
+        constexpr int TL = L / E;
+        constexpr bool LAST = (S + 1 == NST);
+        static_assert(E % R == 0, "radix must divide the points per thread");
+        fft_stage_ct<R, INV, LAST, TL, NS, L / (NS * R)>(v, t, tw, sm, map, active);
+        if constexpr (!LAST) {
+            __syncthreads();
+            if (active) {
+#pragma unroll
+                for (int m = 0; m < E; ++m) v[m] = sm[map(t + m * TL)];
+            }
+            __syncthreads();
+            line_fft_ct_from<INV, L, S + 1>(v, t, tw, sm, map, active);
+        }
+    }
+}
+
+// As line_fft_ct_from, but stage s writes its outputs to bufs[(PAR + s) & 1]
+// and needs a single barrier per exchange: a buffer is written again only two
+// exchanges later, after every thread has passed the barrier that follows its
+// last read of it.  The caller must not read either buffer concurrently with
+// the first exchange's writes to bufs[PAR].
+template <bool INV, int L, int S, int PAR, int E, typename C, typename Map>
+__device__ __forceinline__ void line_fft_ct_db(C (&v)[E], int t, const C *__restrict__ tw, C *buf0, C *buf1,
+                                               const Map &map)
+{
+    constexpr int NST = ct_nst(L, E);
+    if constexpr (S < NST) {
+        constexpr int R = ct_radix(L, S, E);
+        constexpr int NS = ct_ns(L, S, E);
+        constexpr int TL = L / E;
+        constexpr bool LAST = (S + 1 == NST);
+        C *sm = ((PAR + S) & 1) ? buf1 : buf0;
+        fft_stage_ct<R, INV, LAST, TL, NS, L / (NS * R)>(v, t, tw, sm, map, true);
+        if constexpr (!LAST) {
+            __syncthreads();
+#pragma unroll
+            for (int m = 0; m < E; ++m) v[m] = sm[map(t + m * TL)];
+            line_fft_ct_db<INV, L, S + 1, PAR>(v, t, tw, buf0, buf1, map);
+        }
+    }
+}
+
+// Number of exchanges (shared-memory round trips) of an L-point line.
+constexpr int ct_exchanges(int L, int E) { return ct_nst(L, E) - 1; }
+
+// Line transform with a compile-time plan when LC > 0, else the run-time plan.
+template <bool INV, int LC, int E, typename C, typename Map>
+__device__ __forceinline__ void line_fft_any(C (&v)[E], int t, const LinePlan &pl, const C *__restrict__ tw,
+                                             C *sm, const Map &map, bool active)
+{
+    if constexpr (LC > 0) {
+        static_assert(ct_E(LC) == E, "compile-time plan needs its own points per thread");
+        line_fft_ct_from<INV, LC, 0>(v, t, tw, sm, map, active);
+    } else {
+        line_fft<INV>(v, t, pl, tw, sm, map, active);
     }
 }
 

@@ -2,6 +2,8 @@
 // compiled in parallel).  Each picks the instantiation for E at run time.
 #pragma once
 
+#include <cuda.h>
+
 #include "passes.cuh"
 
 namespace psolve {
@@ -24,6 +26,29 @@ cudaError_t launch_ypass(const SArgs<T> &a, bool inverse, unsigned grid, unsigne
                          cudaStream_t s);
 template <typename T>
 cudaError_t launch_xfused(const XArgs<T> &a, unsigned grid, unsigned block, size_t smem, cudaStream_t s);
+
+// Persistent TMA-fed FP32 y/x passes for lines of 256, 512 or 1024 points.
+struct TmaArgs {
+    float2 *data;          // packed spectrum
+    int M, ny, ncb;        // columns per row, rows per plane, column tiles per row
+    long long main_tiles;  // y: planes·ncb; x: instances·ny·ncb
+    long long sInst;       // complex elements per instance
+    long long npairs;      // x: instances·(ny/2 + 1)
+    const float2 *tw;      // e^{-2πi j/L}
+    float coef;            // 1 / (4π² N)
+    int *status;           // device status word
+    LinePlan pl_x;         // run-time plan of the x line (packed-column pairs)
+};
+bool tma_supported(int L);
+// cfg 0: 64 KiB tiles, 16 points per thread, one 512-thread block per SM;
+// cfg 1: 32 KiB tiles, 16 points per thread, 256-thread blocks, two per SM;
+// cfg 2: 32 KiB tiles, 8 points per thread, 512-thread blocks, two per SM.
+int tma_columns(int L, int cfg);
+int tma_threads(int L, int cfg);
+size_t tma_smem_bytes(int L, int cfg);
+// kind: 0 = y forward, 1 = y inverse, 2 = x with the spectral division.
+cudaError_t launch_strided_tma(const CUtensorMap &map, const TmaArgs &a, int L, int kind, int cfg,
+                               unsigned grid, cudaStream_t s);
 
 // Twiddles e^{-2πi j/denom}, j < count, computed in FP64 and rounded to T.
 template <typename T>

@@ -20,6 +20,10 @@
 
 #include "fft_core.cuh"
 
+#ifndef PSOLVE_CT_MINB
+#define PSOLVE_CT_MINB 2
+#endif
+
 namespace psolve {
 
 template <typename T> struct ZArgs {
@@ -58,27 +62,30 @@ template <typename T> struct XArgs {
 };
 
 // Launch bound per instantiation: the host mirrors this in max_threads().
-template <typename T, int E> struct Bound {
+// Compile-time-plan (LC > 0) FP32 kernels ask for two resident blocks.
+template <typename T, int E, int LC> struct Bound {
     static constexpr int value = (sizeof(T) == 8 || E > 16) ? 256 : 512;
+    static constexpr int minb = (LC > 0 && sizeof(T) == 4) ? PSOLVE_CT_MINB : 1;
 };
 
 // --------------------------------------------------------------- z forward
-template <typename T, int E>
-__global__ void __launch_bounds__(Bound<T, E>::value) k_zfwd(ZArgs<T> a)
+template <typename T, int E, int LC>
+__global__ void __launch_bounds__(Bound<T, E, LC>::value, Bound<T, E, LC>::minb) k_zfwd(ZArgs<T> a)
 {
     using C = typename cplx_of<T>::type;
     extern __shared__ __align__(16) unsigned char smraw[];
     C *stw = reinterpret_cast<C *>(smraw);
-    C *sx = stw + a.M;
-    const int TL = a.pl.TL;
+    const int M = LC > 0 ? LC : a.M;
+    C *sx = stw + M;
+    const int TL = LC > 0 ? LC / E : a.pl.TL;
     const int tid = threadIdx.x;
     const int w = tid / TL, t = tid - w * TL;
     const long long row = (long long)blockIdx.x * a.W + w;
     const bool active = (w < a.W) && (row < a.rows);
-    for (int i = tid; i < a.M; i += blockDim.x) stw[i] = a.tw[i];
+    for (int i = tid; i < M; i += blockDim.x) stw[i] = a.tw[i];
     C v[E];
     if (active) {
-        const C *src = reinterpret_cast<const C *>(a.in + row * a.nz) + t;
+        const C *src = reinterpret_cast<const C *>(a.in + row * (2 * M)) + t;
 #pragma unroll
         for (int m = 0; m < E; ++m) v[m] = src[m * TL];
     } else {
@@ -86,9 +93,9 @@ __global__ void __launch_bounds__(Bound<T, E>::value) k_zfwd(ZArgs<T> a)
         for (int m = 0; m < E; ++m) v[m] = C{0, 0};
     }
     __syncthreads();
-    const int LP = a.M + (a.M >> 4) + 1;
+    const int LP = M + (M >> 4) + 1;
     const MapRow map{w * LP};
-    line_fft<false>(v, t, a.pl, stw, sx, map, active);
+    line_fft_any<false, LC>(v, t, a.pl, stw, sx, map, active);
     // Z[k] -> X[k] needs Z[M-k]: exchange through shared memory.
     if (active) {
 #pragma unroll
@@ -96,7 +103,7 @@ __global__ void __launch_bounds__(Bound<T, E>::value) k_zfwd(ZArgs<T> a)
     }
     __syncthreads();
     if (active) {
-        C *dst = reinterpret_cast<C *>(a.out) + row * a.M;
+        C *dst = reinterpret_cast<C *>(a.out) + row * M;
         const T half = (T)0.5;
 #pragma unroll
         for (int m = 0; m < E; ++m) {
@@ -105,7 +112,7 @@ __global__ void __launch_bounds__(Bound<T, E>::value) k_zfwd(ZArgs<T> a)
             if (k == 0) {
                 dst[0] = C{z.x + z.y, z.x - z.y}; // X[0] + i X[M]
             } else {
-                const C zp = sx[map(a.M - k)];
+                const C zp = sx[map(M - k)];
                 const C e = {(z.x + zp.x) * half, (z.y - zp.y) * half};   // (Z + conj Zp)/2
                 const C o = {(z.y + zp.y) * half, (zp.x - z.x) * half};   // (Z - conj Zp)/(2i)
                 dst[k] = cadd(e, cmul(o, a.post[k]));
@@ -115,30 +122,40 @@ __global__ void __launch_bounds__(Bound<T, E>::value) k_zfwd(ZArgs<T> a)
 }
 
 // --------------------------------------------------------------- z inverse
-template <typename T, int E>
-__global__ void __launch_bounds__(Bound<T, E>::value) k_zinv(ZArgs<T> a)
+template <typename T, int E, int LC>
+__global__ void __launch_bounds__(Bound<T, E, LC>::value, Bound<T, E, LC>::minb) k_zinv(ZArgs<T> a)
 {
     using C = typename cplx_of<T>::type;
     extern __shared__ __align__(16) unsigned char smraw[];
     C *stw = reinterpret_cast<C *>(smraw);
-    C *sx = stw + a.M;
-    const int TL = a.pl.TL;
+    const int M = LC > 0 ? LC : a.M;
+    C *sx = stw + M;
+    const int TL = LC > 0 ? LC / E : a.pl.TL;
     const int tid = threadIdx.x;
     const int w = tid / TL, t = tid - w * TL;
     const long long row = (long long)blockIdx.x * a.W + w;
     const bool active = (w < a.W) && (row < a.rows);
-    for (int i = tid; i < a.M; i += blockDim.x) stw[i] = a.tw[i];
+    for (int i = tid; i < M; i += blockDim.x) stw[i] = a.tw[i];
     C v[E];
+    const int LP = M + (M >> 4) + 1;
+    const MapRow map{w * LP};
     if (active) {
-        const C *src = reinterpret_cast<const C *>(a.in) + row * a.M;
+        const C *src = reinterpret_cast<const C *>(a.in) + row * M + t;
+#pragma unroll
+        for (int m = 0; m < E; ++m) v[m] = src[m * TL];
+#pragma unroll
+        for (int m = 0; m < E; ++m) sx[map(t + m * TL)] = v[m];
+    }
+    __syncthreads(); // the whole row is in registers and shared memory (in place)
+    if (active) {
 #pragma unroll
         for (int m = 0; m < E; ++m) {
             const int k = t + m * TL;
-            const C x = src[k];
+            const C x = v[m];
             if (k == 0) {
                 v[m] = C{x.x + x.y, x.x - x.y};
             } else {
-                const C xp = src[a.M - k];
+                const C xp = sx[map(M - k)];
                 const C e = {x.x + xp.x, x.y - xp.y};                  // X + conj Xp
                 const C o = cmulc(C{x.x - xp.x, x.y + xp.y}, a.post[k]); // (X - conj Xp) e^{+2πik/nz}
                 v[m] = C{e.x - o.y, e.y + o.x};                        // E + i O
@@ -148,26 +165,25 @@ __global__ void __launch_bounds__(Bound<T, E>::value) k_zinv(ZArgs<T> a)
 #pragma unroll
         for (int m = 0; m < E; ++m) v[m] = C{0, 0};
     }
-    __syncthreads(); // every load of the row precedes any store (in place)
-    const int LP = a.M + (a.M >> 4) + 1;
-    const MapRow map{w * LP};
-    line_fft<true>(v, t, a.pl, stw, sx, map, active);
+    __syncthreads(); // partner reads done before the transform reuses the buffer
+    line_fft_any<true, LC>(v, t, a.pl, stw, sx, map, active);
     if (active) {
-        C *dst = reinterpret_cast<C *>(a.out + row * a.nz) + t;
+        C *dst = reinterpret_cast<C *>(a.out + row * (2 * M)) + t;
 #pragma unroll
         for (int m = 0; m < E; ++m) dst[m * TL] = v[m];
     }
 }
 
 // ------------------------------------------------------- strided c2c (y)
-template <typename T, int E, bool INV>
-__global__ void __launch_bounds__(Bound<T, E>::value) k_ypass(SArgs<T> a)
+template <typename T, int E, bool INV, int LC>
+__global__ void __launch_bounds__(Bound<T, E, LC>::value, Bound<T, E, LC>::minb) k_ypass(SArgs<T> a)
 {
     using C = typename cplx_of<T>::type;
     extern __shared__ __align__(16) unsigned char smraw[];
     C *stw = reinterpret_cast<C *>(smraw);
-    C *sx = stw + a.pl.L;
-    const int W = a.W, TL = a.pl.TL;
+    const int L = LC > 0 ? LC : a.pl.L;
+    C *sx = stw + L;
+    const int W = a.W, TL = LC > 0 ? LC / E : a.pl.TL;
     const int tid = threadIdx.x;
     const int w = tid % W, t = tid / W;
     const long long tile = blockIdx.x;
@@ -175,7 +191,7 @@ __global__ void __launch_bounds__(Bound<T, E>::value) k_ypass(SArgs<T> a)
     const long long plane = tile / a.ncb;
     const int col = cb * W + w;
     const bool active = col < a.M;
-    for (int i = tid; i < a.pl.L; i += blockDim.x) stw[i] = a.tw[i];
+    for (int i = tid; i < L; i += blockDim.x) stw[i] = a.tw[i];
     C *base = reinterpret_cast<C *>(a.data) + plane * a.sPlane + col + (long long)t * a.sL;
     const long long step = (long long)TL * a.sL;
     C v[E];
@@ -188,22 +204,92 @@ __global__ void __launch_bounds__(Bound<T, E>::value) k_ypass(SArgs<T> a)
     }
     __syncthreads();
     const MapStrided map{W, w};
-    line_fft<INV>(v, t, a.pl, stw, sx, map, active);
+    line_fft_any<INV, LC>(v, t, a.pl, stw, sx, map, active);
     if (active) {
 #pragma unroll
         for (int m = 0; m < E; ++m) base[m * step] = v[m];
     }
 }
 
+// Packed column kz = 0 holds X0 + i·XM for every (x, y) line.  After the
+// 2D (y, x) transform H = G0 + i·G1 with G0, G1 the spectra of two real
+// planes, so G0(k) = (H(k) + conj H(-k))/2, G1(k) = (H(k) - conj H(-k))/(2i).
+// Each is scaled by its own symbol (kz = 0 and kz = M) and recombined:
+//   H'(k) = ((D0 + D1)/2) H(k) + ((D0 - D1)/2) conj H(-k).
+// Lines 2q and 2q+1 of the block hold rows ky and (ny - ky) mod ny; block
+// `pidx` takes pairs pidx·(W/2) .. pidx·(W/2) + W/2 - 1.  All threads of the
+// block must call it (it synchronises).
+template <typename T, int E, int LC>
+__device__ __forceinline__ void xpair_block(T *data, int nx_rt, int ny, int M, long long sInst, long long npairs,
+                                            T coef, const LinePlan &pl, int W, int TL, long long pidx, int t,
+                                            int w, const typename cplx_of<T>::type *stw,
+                                            typename cplx_of<T>::type *sx)
+{
+    using C = typename cplx_of<T>::type;
+    const int nx = LC > 0 ? LC : nx_rt;
+    const long long sL = (long long)ny * M;
+    const long long step = (long long)TL * sL;
+    const MapStrided map{W, w};
+    C v[E];
+    const int half = W >> 1;
+    const int q = w >> 1, side = w & 1;
+    const long long pair = pidx * half + q;
+    const bool active = (w < 2 * half) && (pair < npairs);
+    const int per = ny / 2 + 1;
+    const long long b = active ? pair / per : 0;
+    const int ky = active ? (int)(pair % per) : 0;
+    const int row = side ? (ny - ky) % ny : ky;
+    C *base = reinterpret_cast<C *>(data) + b * sInst + (long long)row * M + (long long)t * sL;
+    if (active) {
+#pragma unroll
+        for (int m = 0; m < E; ++m) v[m] = base[m * step];
+    } else {
+#pragma unroll
+        for (int m = 0; m < E; ++m) v[m] = C{0, 0};
+    }
+    __syncthreads();
+    line_fft_any<false, LC>(v, t, pl, stw, sx, map, active);
+    if (active) {
+#pragma unroll
+        for (int m = 0; m < E; ++m) sx[map(t + m * TL)] = v[m];
+    }
+    __syncthreads();
+    if (active) {
+        const int kys = kvec_dev(row, ny);
+        const int partner = w ^ 1;
+#pragma unroll
+        for (int m = 0; m < E; ++m) {
+            const int jx = t + m * TL;
+            const int jm = (jx == 0) ? 0 : nx - jx;
+            const C h1 = v[m];
+            const C h2 = sx[jm * W + partner];
+            const int kx = kvec_dev(jx, nx);
+            const int k2a = kx * kx + kys * kys;
+            const int k2b = k2a + M * M;
+            const T d0 = (k2a == 0) ? (T)0 : coef / (T)k2a;
+            const T d1 = coef / (T)k2b;
+            const T sp = (d0 + d1) * (T)0.5, sm = (d0 - d1) * (T)0.5;
+            v[m] = C{sp * h1.x + sm * h2.x, sp * h1.y - sm * h2.y};
+        }
+    }
+    __syncthreads();
+    line_fft_any<true, LC>(v, t, pl, stw, sx, map, active);
+    if (active && !(side == 1 && row == ky)) {
+#pragma unroll
+        for (int m = 0; m < E; ++m) base[m * step] = v[m];
+    }
+}
+
 // ----------------------------------- x forward, spectral division, x inverse
-template <typename T, int E>
-__global__ void __launch_bounds__(Bound<T, E>::value) k_xfused(XArgs<T> a)
+template <typename T, int E, int LC>
+__global__ void __launch_bounds__(Bound<T, E, LC>::value, Bound<T, E, LC>::minb) k_xfused(XArgs<T> a)
 {
     using C = typename cplx_of<T>::type;
     extern __shared__ __align__(16) unsigned char smraw[];
     C *stw = reinterpret_cast<C *>(smraw);
-    C *sx = stw + a.pl.L;
-    const int W = a.W, TL = a.pl.TL, nx = a.nx, ny = a.ny, M = a.M;
+    const int nx = LC > 0 ? LC : a.nx;
+    C *sx = stw + nx;
+    const int W = a.W, TL = LC > 0 ? LC / E : a.pl.TL, ny = a.ny, M = a.M;
     const int tid = threadIdx.x;
     const int w = tid % W, t = tid / W;
     const long long tile = blockIdx.x;
@@ -229,7 +315,7 @@ __global__ void __launch_bounds__(Bound<T, E>::value) k_xfused(XArgs<T> a)
             for (int m = 0; m < E; ++m) v[m] = C{0, 0};
         }
         __syncthreads();
-        line_fft<false>(v, t, a.pl, stw, sx, map, active);
+        line_fft_any<false, LC>(v, t, a.pl, stw, sx, map, active);
         const int ky = kvec_dev(y, ny);
         const int kyz = ky * ky + col * col;
 #pragma unroll
@@ -239,7 +325,7 @@ __global__ void __launch_bounds__(Bound<T, E>::value) k_xfused(XArgs<T> a)
             const T d = (k2 == 0) ? (T)0 : a.coef / (T)k2;
             v[m] = cscale(v[m], d);
         }
-        line_fft<true>(v, t, a.pl, stw, sx, map, active);
+        line_fft_any<true, LC>(v, t, a.pl, stw, sx, map, active);
         if (active && col != 0) {
 #pragma unroll
             for (int m = 0; m < E; ++m) base[m * step] = v[m];
@@ -247,60 +333,8 @@ __global__ void __launch_bounds__(Bound<T, E>::value) k_xfused(XArgs<T> a)
         return;
     }
 
-    // Packed column kz = 0 holds X0 + i·XM for every (x, y) line.  After the
-    // 2D (y, x) transform H = G0 + i·G1 with G0, G1 the spectra of two real
-    // planes, so G0(k) = (H(k) + conj H(-k))/2, G1(k) = (H(k) - conj H(-k))/(2i).
-    // Each is scaled by its own symbol (kz = 0 and kz = M) and recombined:
-    //   H'(k) = ((D0 + D1)/2) H(k) + ((D0 - D1)/2) conj H(-k).
-    // Lines 2q and 2q+1 of the block hold rows ky and (ny - ky) mod ny.
-    const long long pidx = tile - a.main_tiles;
-    const int half = W >> 1;
-    const int q = w >> 1, side = w & 1;
-    const long long pair = pidx * half + q;
-    const bool active = (w < 2 * half) && (pair < a.npairs);
-    const int per = ny / 2 + 1;
-    const long long b = active ? pair / per : 0;
-    const int ky = active ? (int)(pair % per) : 0;
-    const int row = side ? (ny - ky) % ny : ky;
-    C *base = reinterpret_cast<C *>(a.data) + b * a.sInst + (long long)row * M + (long long)t * sL;
-    if (active) {
-#pragma unroll
-        for (int m = 0; m < E; ++m) v[m] = base[m * step];
-    } else {
-#pragma unroll
-        for (int m = 0; m < E; ++m) v[m] = C{0, 0};
-    }
-    __syncthreads();
-    line_fft<false>(v, t, a.pl, stw, sx, map, active);
-    if (active) {
-#pragma unroll
-        for (int m = 0; m < E; ++m) sx[map(t + m * TL)] = v[m];
-    }
-    __syncthreads();
-    if (active) {
-        const int kys = kvec_dev(row, ny);
-        const int partner = w ^ 1;
-#pragma unroll
-        for (int m = 0; m < E; ++m) {
-            const int jx = t + m * TL;
-            const int jm = (jx == 0) ? 0 : nx - jx;
-            const C h1 = v[m];
-            const C h2 = sx[jm * W + partner];
-            const int kx = kvec_dev(jx, nx);
-            const int k2a = kx * kx + kys * kys;
-            const int k2b = k2a + M * M;
-            const T d0 = (k2a == 0) ? (T)0 : a.coef / (T)k2a;
-            const T d1 = a.coef / (T)k2b;
-            const T sp = (d0 + d1) * (T)0.5, sm = (d0 - d1) * (T)0.5;
-            v[m] = C{sp * h1.x + sm * h2.x, sp * h1.y - sm * h2.y};
-        }
-    }
-    __syncthreads();
-    line_fft<true>(v, t, a.pl, stw, sx, map, active);
-    if (active && !(side == 1 && row == ky)) {
-#pragma unroll
-        for (int m = 0; m < E; ++m) base[m * step] = v[m];
-    }
+    xpair_block<T, E, LC>(a.data, nx, ny, M, a.sInst, a.npairs, a.coef, a.pl, W, TL, tile - a.main_tiles, t,
+                          w, stw, sx);
 }
 
 } // namespace psolve

@@ -15,16 +15,25 @@ static cudaError_t run(K kernel, const ZArgs<T> &a, unsigned grid, unsigned bloc
     return cudaGetLastError();
 }
 
+// Compile-time plans for the hot FP32 row lengths, the run-time plan otherwise.
 #define PSOLVE_Z_DISPATCH(KERNEL)                                                   \
+    if constexpr (sizeof(T) == 4) if (a.pl.E == 16) {                               \
+        switch (a.pl.L) {                                                           \
+        case 256: return run<T, 16>(KERNEL<T, 16, 256>, a, grid, block, smem, s);   \
+        case 512: return run<T, 16>(KERNEL<T, 16, 512>, a, grid, block, smem, s);   \
+        case 1024: return run<T, 16>(KERNEL<T, 16, 1024>, a, grid, block, smem, s); \
+        default: break;                                                             \
+        }                                                                           \
+    }                                                                               \
     switch (a.pl.E) {                                                               \
-    case 2: return run<T, 2>(KERNEL<T, 2>, a, grid, block, smem, s);                \
-    case 3: return run<T, 3>(KERNEL<T, 3>, a, grid, block, smem, s);                \
-    case 4: return run<T, 4>(KERNEL<T, 4>, a, grid, block, smem, s);                \
-    case 6: return run<T, 6>(KERNEL<T, 6>, a, grid, block, smem, s);                \
-    case 8: return run<T, 8>(KERNEL<T, 8>, a, grid, block, smem, s);                \
-    case 12: return run<T, 12>(KERNEL<T, 12>, a, grid, block, smem, s);             \
-    case 16: return run<T, 16>(KERNEL<T, 16>, a, grid, block, smem, s);             \
-    case 24: return run<T, 24>(KERNEL<T, 24>, a, grid, block, smem, s);             \
+    case 2: return run<T, 2>(KERNEL<T, 2, 0>, a, grid, block, smem, s);             \
+    case 3: return run<T, 3>(KERNEL<T, 3, 0>, a, grid, block, smem, s);             \
+    case 4: return run<T, 4>(KERNEL<T, 4, 0>, a, grid, block, smem, s);             \
+    case 6: return run<T, 6>(KERNEL<T, 6, 0>, a, grid, block, smem, s);             \
+    case 8: return run<T, 8>(KERNEL<T, 8, 0>, a, grid, block, smem, s);             \
+    case 12: return run<T, 12>(KERNEL<T, 12, 0>, a, grid, block, smem, s);          \
+    case 16: return run<T, 16>(KERNEL<T, 16, 0>, a, grid, block, smem, s);          \
+    case 24: return run<T, 24>(KERNEL<T, 24, 0>, a, grid, block, smem, s);          \
     default: return cudaErrorInvalidValue;                                          \
     }
 

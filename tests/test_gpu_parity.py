@@ -51,6 +51,29 @@ def test_random_field_parity(prec, shape):
     assert err <= TOL[prec], (shape, prec, err)
 
 
+# Lines of 256/512/1024 points go through the persistent TMA-fed y/x passes
+# in FP32 (column tiles of 32/16/8); 96 and 48 leave a ragged last tile.
+TMA_SHAPES = [(256, 512, 96), (512, 256, 32), (1024, 256, 16), (256, 1024, 48), (512, 512, 64),
+              (256, 256, 256)]
+
+
+@pytest.mark.parametrize("shape", TMA_SHAPES)
+def test_tma_pass_parity_fp32(shape):
+    f64 = wl.random_field(shape, seed=300 + sum(shape))
+    u, f_in = gpu_solve(f64, "f32")
+    ref = oracle.solve(f_in.astype(np.float64))
+    err = oracle.rel_l2(u, ref)
+    assert err <= TOL["f32"], (shape, err)
+
+
+def test_tma_pass_batch_fp32():
+    shape, B = (256, 256, 32), 3
+    f = np.stack([wl.random_field(shape, seed=70 + b) for b in range(B)])
+    u, f_in = gpu_solve(f, "f32", batch=B)
+    for b in range(B):
+        assert oracle.rel_l2(u[b], oracle.solve(f_in[b].astype(np.float64))) <= TOL["f32"]
+
+
 def test_config1_fp64_mode_sum_closed_form():
     w = wl.mode_sum()
     u, _ = gpu_solve(w.f, "f64")
