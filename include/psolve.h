@@ -128,8 +128,21 @@ psolve_status psolve_pass_times(psolve_plan *plan, double *ms, int cap, int *n_p
  * "zinv"), or NULL. */
 const char *psolve_pass_name(const psolve_plan *plan, int i);
 
-/* Number of kernel launches one psolve_execute enqueues; 0 on error. */
+/* Number of kernel launches one psolve_execute enqueues; 0 on error.  A plan
+ * of unequal grids (psolve_plan_create_many) runs every pass of every
+ * instance in ONE persistent kernel launched from a CUDA graph (a memset
+ * node zeroes its work counters first), and its profile has a single pass
+ * named "batched". */
 int psolve_launches_per_solve(const psolve_plan *plan);
+
+/* Test hook for the persistent batched launch: its blocks wait for the
+ * tiles of an instance's previous pass with a time limit of wait_ns
+ * nanoseconds (default 2 s), after which they record PSOLVE_ERR_TIMEOUT in
+ * the status word (read by psolve_get_status) and exit; the GPU context stays
+ * usable.  unsatisfiable = 1 makes pass 1 of instance 0 wait for one more
+ * tile than pass 0 has, so that wait must run out; 0 restores it.
+ * PSOLVE_ERR_INVALID_ARG for a plan without the batched launch. */
+psolve_status psolve_debug_set_wait(psolve_plan *plan, unsigned long long wait_ns, int unsatisfiable);
 
 /* Allocation-free solve, for callers that cannot allocate device memory:
  * code inside a custom allocator or memory-pool callback, frameworks that

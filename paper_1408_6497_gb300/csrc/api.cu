@@ -203,6 +203,22 @@ struct psolve_plan {
     int *status;
     void *stage;
     size_t stage_bytes;
+    // persistent batched path (plans of unequal grids)
+    bool batched;
+    void *segs_dev;                 // BatchSeg<T>[nseg]
+    std::vector<unsigned char> segs_host;
+    int nseg;
+    long long total_items;
+    size_t batch_smem;
+    unsigned grid_batched;
+    void *counters;                 // work counter (8 B) + done[nseg]
+    cudaGraph_t graph;
+    cudaGraphExec_t gexec;
+    cudaGraphNode_t knode;
+    const void *g_f;
+    void *g_u;
+    unsigned long long wait_ns;
+    unsigned long long g_wait;
     // per-pass profiling: one set of kPasses+1 events per recorded solve
     bool profiling;
     std::vector<std::vector<cudaEvent_t>> ev_used;
@@ -264,11 +280,117 @@ void release(psolve_plan *p)
 {
     if (!p) return;
     destroy_events(p);
+    if (p->gexec) cudaGraphExecDestroy(p->gexec);
+    if (p->graph) cudaGraphDestroy(p->graph);
+    if (p->segs_dev) cudaFree(p->segs_dev);
+    if (p->counters) cudaFree(p->counters);
     if (p->tables) cudaFree(p->tables);
     if (p->status) cudaFree(p->status);
     if (p->stage) cudaFree(p->stage);
     p->magic = 0;
     delete p;
+}
+
+// Segments of the persistent batched launch: pass-major, one per (pass,
+// instance), each with a tile width that fits kBatchThreads threads.
+template <typename T> psolve_status setup_batched(psolve_plan *p)
+{
+    using C = typename cplx_of<T>::type;
+    const C *tab = reinterpret_cast<const C *>(p->tables);
+    const int B = (int)p->groups.size();
+    const size_t cs = sizeof(C);
+    const int NT = kBatchThreads;
+    std::vector<BatchSeg<T>> segs(5 * (size_t)B);
+    long long first = 0;
+    size_t smem = 0;
+    for (int pass = 0; pass < 5; ++pass) {
+        for (int i = 0; i < B; ++i) {
+            const Group &g = p->groups[i];
+            BatchSeg<T> sg;
+            std::memset(&sg, 0, sizeof(sg));
+            sg.kind = pass;
+            sg.dep = pass == 0 ? -1 : (pass - 1) * B + i;
+            sg.off = (long long)g.off0;
+            const int M = g.M;
+            if (pass == 0 || pass == 4) {
+                int W = std::max(1, NT / g.pz.TL);
+                const int LP = M + (M >> 4) + 1;
+                while (W > 1 && (size_t)(M + (size_t)W * LP) * cs > kSmemCap) W /= 2;
+                sg.E = g.pz.E;
+                sg.z.rows = (long long)g.nx * g.ny;
+                sg.z.nz = g.nz;
+                sg.z.M = M;
+                sg.z.W = W;
+                sg.z.pl = g.pz;
+                sg.z.tw = tab + g.tw_z;
+                sg.z.post = tab + g.post;
+                sg.ntiles = (sg.z.rows + W - 1) / W;
+                smem = std::max(smem, (size_t)(M + (size_t)W * LP) * cs);
+            } else if (pass == 1 || pass == 3) {
+                int W = std::min(M, std::max(1, NT / g.py.TL));
+                while (W > 1 && s_smem(g.ny, W, p->dtype) > kSmemCap) W /= 2;
+                sg.E = g.py.E;
+                sg.y.nplanes = g.nx;
+                sg.y.sPlane = (long long)g.ny * M;
+                sg.y.sL = M;
+                sg.y.M = M;
+                sg.y.W = W;
+                sg.y.ncb = (M + W - 1) / W;
+                sg.y.pl = g.py;
+                sg.y.tw = tab + g.tw_y;
+                sg.ntiles = (long long)g.nx * sg.y.ncb;
+                smem = std::max(smem, s_smem(g.ny, W, p->dtype));
+            } else {
+                int W = std::max(2, std::min(std::max(2, M), NT / g.px.TL));
+                while (W > 2 && s_smem(g.nx, W, p->dtype) > kSmemCap) W /= 2;
+                if (W * g.px.TL > NT) return fail(PSOLVE_ERR_UNSUPPORTED_SIZE, "x line too long for a batch tile");
+                sg.E = g.px.E;
+                sg.x.batch = 1;
+                sg.x.nx = g.nx;
+                sg.x.ny = g.ny;
+                sg.x.M = M;
+                sg.x.sInst = (long long)g.nx * g.ny * M;
+                sg.x.W = W;
+                sg.x.ncb = (M + W - 1) / W;
+                sg.x.main_tiles = (long long)g.ny * sg.x.ncb;
+                sg.x.npairs = g.ny / 2 + 1;
+                sg.x.pl = g.px;
+                sg.x.tw = tab + g.tw_x;
+                sg.x.coef = (T)(1.0 / (4.0 * M_PI * M_PI * ((double)g.nx * g.ny * g.nz)));
+                sg.ntiles = sg.x.main_tiles + (sg.x.npairs + W / 2 - 1) / (W / 2);
+                smem = std::max(smem, s_smem(g.nx, W, p->dtype));
+            }
+            sg.first = first;
+            first += sg.ntiles;
+            segs[(size_t)pass * B + i] = sg;
+        }
+    }
+    for (auto &sg : segs)
+        if (sg.dep >= 0) sg.need = (int)segs[sg.dep].ntiles;
+    p->nseg = (int)segs.size();
+    p->total_items = first;
+    p->batch_smem = smem;
+    const size_t bytes = segs.size() * sizeof(BatchSeg<T>);
+    p->segs_host.assign(reinterpret_cast<unsigned char *>(segs.data()),
+                        reinterpret_cast<unsigned char *>(segs.data()) + bytes);
+    if (cudaMalloc(&p->segs_dev, bytes) != cudaSuccess) {
+        p->segs_dev = nullptr;
+        return fail(PSOLVE_ERR_OOM, "batch segment table");
+    }
+    if (cudaMalloc(&p->counters, 8 + 4 * (size_t)p->nseg) != cudaSuccess) {
+        p->counters = nullptr;
+        return fail(PSOLVE_ERR_OOM, "batch counters");
+    }
+    cudaError_t e = cudaMemcpy(p->segs_dev, segs.data(), bytes, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "upload batch segments");
+    e = batched_prepare<T>(smem);
+    if (e != cudaSuccess) return cuda_fail(e, "batched kernel attributes");
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_kernel<T>(), kBatchThreads, smem);
+    if (e != cudaSuccess || per_sm < 1) return cuda_fail(e, "batched kernel occupancy");
+    p->grid_batched = (unsigned)std::min<long long>(first, (long long)p->num_sms * per_sm);
+    p->batched = true;
+    return PSOLVE_OK;
 }
 
 psolve_status build_plan(const std::vector<int> &nx, const std::vector<int> &ny, const std::vector<int> &nz,
@@ -285,6 +407,20 @@ psolve_status build_plan(const std::vector<int> &nx, const std::vector<int> &ny,
     p->stage = nullptr;
     p->stage_bytes = 0;
     p->profiling = false;
+    p->batched = false;
+    p->segs_dev = nullptr;
+    p->counters = nullptr;
+    p->graph = nullptr;
+    p->gexec = nullptr;
+    p->knode = nullptr;
+    p->g_f = nullptr;
+    p->g_u = nullptr;
+    p->nseg = 0;
+    p->total_items = 0;
+    p->batch_smem = 0;
+    p->grid_batched = 0;
+    p->wait_ns = 2000000000ull;
+    p->g_wait = 0;
     size_t off = 0;
     for (int b = 0; b < batch; ++b) {
         const size_t N = (size_t)nx[b] * ny[b] * nz[b];
@@ -370,6 +506,21 @@ psolve_status build_plan(const std::vector<int> &nx, const std::vector<int> &ny,
     }
     e = cudaDeviceSynchronize();
     if (e != cudaSuccess) { release(p.release()); return cuda_fail(e, "plan set-up"); }
+    if (!uniform) {
+        const char *env = std::getenv("PSOLVE_BATCHED");
+        if (!(env && env[0] == '0')) {
+            bool ok = dtype != PSOLVE_F64;
+            for (const auto &g : p->groups)
+                ok = ok && batched_supports_E(g.pz.E) && batched_supports_E(g.py.E) && batched_supports_E(g.px.E);
+            if (ok) {
+                psolve_status st = setup_batched<float>(p.get());
+                if (st != PSOLVE_OK) {
+                    release(p.release());
+                    return st;
+                }
+            }
+        }
+    }
     *out = p.release();
     return PSOLVE_OK;
 }
@@ -566,6 +717,62 @@ psolve_status check_buffers(const psolve_plan *p, const void *f, const void *u)
     return PSOLVE_OK;
 }
 
+// One graph: zero the counters, then the persistent kernel.  Built on first
+// use; later solves only rewrite the kernel node's f/u pointers.
+psolve_status run_batched(psolve_plan *p, const void *f, void *u, cudaStream_t s)
+{
+    int *status = p->status;
+    unsigned long long *work = reinterpret_cast<unsigned long long *>(p->counters);
+    int *done = reinterpret_cast<int *>(reinterpret_cast<char *>(p->counters) + 8);
+    const void *segs = p->segs_dev;
+    int nseg = p->nseg;
+    long long total = p->total_items;
+    const void *fa = f;
+    void *ua = u;
+    unsigned long long wait = p->wait_ns;
+    void *args[] = {(void *)&segs, (void *)&nseg, (void *)&total, (void *)&fa, (void *)&ua,
+                    (void *)&work, (void *)&done, (void *)&status, (void *)&wait};
+    cudaKernelNodeParams kp{};
+    kp.func = const_cast<void *>(batched_kernel<float>());
+    kp.gridDim = dim3(p->grid_batched);
+    kp.blockDim = dim3(kBatchThreads);
+    kp.sharedMemBytes = (unsigned)p->batch_smem;
+    kp.kernelParams = args;
+    cudaError_t e;
+    if (!p->gexec) {
+        e = cudaGraphCreate(&p->graph, 0);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGraphCreate");
+        cudaMemsetParams mp{};
+        mp.dst = p->counters;
+        mp.value = 0;
+        mp.elementSize = 4;
+        mp.width = (8 + 4 * (size_t)p->nseg) / 4;
+        mp.height = 1;
+        mp.pitch = 0;
+        cudaGraphNode_t mnode;
+        e = cudaGraphAddMemsetNode(&mnode, p->graph, nullptr, 0, &mp);
+        if (e == cudaSuccess) e = cudaGraphAddKernelNode(&p->knode, p->graph, &mnode, 1, &kp);
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&p->gexec, p->graph, 0);
+        if (e != cudaSuccess) return cuda_fail(e, "build batched graph");
+        p->g_f = f;
+        p->g_u = u;
+        p->g_wait = wait;
+    } else if (p->g_f != f || p->g_u != u || p->g_wait != wait) {
+        e = cudaGraphExecKernelNodeSetParams(p->gexec, p->knode, &kp);
+        if (e != cudaSuccess) return cuda_fail(e, "update batched graph");
+        p->g_f = f;
+        p->g_u = u;
+        p->g_wait = wait;
+    }
+    const std::vector<cudaEvent_t> *ev = take_events(p);
+    if (ev) cudaEventRecord((*ev)[0], s);
+    e = cudaGraphLaunch(p->gexec, s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
+    if (ev)
+        for (int i = 1; i <= kPasses; ++i) cudaEventRecord((*ev)[i], s);
+    return PSOLVE_OK;
+}
+
 psolve_status solve(psolve_plan *p, const void *f, void *u, void *stream)
 {
     if (!plan_ok(p)) return fail(PSOLVE_ERR_INVALID_ARG, "invalid or destroyed plan");
@@ -574,6 +781,7 @@ psolve_status solve(psolve_plan *p, const void *f, void *u, void *stream)
     DeviceGuard dg(p->device);
     if (dg.err != cudaSuccess) return cuda_fail(dg.err, "select device");
     cudaStream_t s = (cudaStream_t)stream;
+    if (p->batched) return run_batched(p, f, u, s);
     for (const auto &g : p->groups) {
         const std::vector<cudaEvent_t> *ev = take_events(p);
         st = p->dtype == PSOLVE_F64
@@ -780,13 +988,37 @@ psolve_status psolve_pass_times(psolve_plan *plan, double *ms, int cap, int *n_p
 const char *psolve_pass_name(const psolve_plan *plan, int i)
 {
     if (!plan_ok(plan) || i < 0 || i >= kPasses) return nullptr;
+    if (plan->batched) return i == 0 ? "batched" : "none";
     return kPassNames[i];
 }
 
 int psolve_launches_per_solve(const psolve_plan *plan)
 {
     if (!plan_ok(plan)) return 0;
+    if (plan->batched) return 1;
     return kPasses * (int)plan->groups.size();
+}
+
+psolve_status psolve_debug_set_wait(psolve_plan *plan, unsigned long long wait_ns, int unsatisfiable)
+{
+    if (!plan_ok(plan)) return fail(PSOLVE_ERR_INVALID_ARG, "invalid or destroyed plan");
+    if (!plan->batched) return fail(PSOLVE_ERR_INVALID_ARG, "plan has no persistent batched launch");
+    DeviceGuard dg(plan->device);
+    plan->wait_ns = wait_ns;
+    // Segment nseg/5 (pass 1 of instance 0) waits on segment 0.
+    const size_t seg_bytes = plan->segs_host.size() / (size_t)plan->nseg;
+    const int target = plan->nseg / 5;
+    unsigned char entry[4096];
+    if (seg_bytes > sizeof(entry)) return fail(PSOLVE_ERR_INTERNAL, "segment too large");
+    std::memcpy(entry, plan->segs_host.data() + (size_t)target * seg_bytes, seg_bytes);
+    int need = 0;
+    std::memcpy(&need, entry + 3 * sizeof(int), sizeof(int));
+    if (unsatisfiable) ++need;
+    std::memcpy(entry + 3 * sizeof(int), &need, sizeof(int));
+    cudaError_t e = cudaMemcpy((char *)plan->segs_dev + (size_t)target * seg_bytes, entry, seg_bytes,
+                               cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "update segment");
+    return PSOLVE_OK;
 }
 
 const char *psolve_status_string(psolve_status s)

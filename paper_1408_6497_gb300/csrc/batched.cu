@@ -1,0 +1,140 @@
+// One persistent launch for a batch of unequal grids.
+//
+// The work list is every tile of every pass of every instance, pass-major:
+// segment s = pass·B + instance holds the tiles of one pass (zfwd, yfwd,
+// xdiv, yinv, zinv) of one instance.  Blocks take items in order from an
+// atomic counter.  Before the first write of segment (pass, i) a block waits
+// until every tile of segment (pass-1, i) has completed: the tiles it waits
+// for have lower item numbers, so they are held by blocks that are already
+// running and never wait on later items; the wait therefore ends unless
+// something is broken, and it is bounded in time all the same (the block
+// then records PSOLVE_ERR_TIMEOUT in the status word and leaves).
+// Data written by other blocks of the same launch are read with L2-only
+// loads (ld.global.cg).  Lines whose points-per-thread is not one of
+// 4, 8, 12, 16, 24 are not covered (the planner then launches per pass).
+#include "psolve.h"
+#include "launch.h"
+#include "tma.cuh"
+
+namespace psolve {
+
+namespace {
+
+__device__ __forceinline__ int ld_acquire(const int *p)
+{
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Wait until *counter >= need, at most limit_ns; false on timeout.
+__device__ bool wait_count(const int *counter, long long need, unsigned long long limit_ns)
+{
+    if (ld_acquire(counter) >= need) return true;
+    const uint64_t t0 = global_ns();
+    while (true) {
+        __nanosleep(256);
+        if (ld_acquire(counter) >= need) return true;
+        if (global_ns() - t0 > limit_ns) return false;
+    }
+}
+
+template <typename T, int E> __device__ __forceinline__ void run_item(const BatchSeg<T> &sg, long long tile,
+                                                                    const T *f, T *u, unsigned char *smem)
+{
+    switch (sg.kind) {
+    case 0: {
+        ZArgs<T> a = sg.z;
+        a.in = f + sg.off;
+        a.out = u + sg.off;
+        zfwd_tile<T, E, 0, true>(a, tile, smem);
+        break;
+    }
+    case 1:
+    case 3: {
+        SArgs<T> a = sg.y;
+        a.data = u + sg.off;
+        if (sg.kind == 1) ypass_tile<T, E, false, 0, true>(a, tile, smem);
+        else ypass_tile<T, E, true, 0, true>(a, tile, smem);
+        break;
+    }
+    case 2: {
+        XArgs<T> a = sg.x;
+        a.data = u + sg.off;
+        xfused_tile<T, E, 0, true>(a, tile, smem);
+        break;
+    }
+    default: {
+        ZArgs<T> a = sg.z;
+        a.in = u + sg.off;
+        a.out = u + sg.off;
+        zinv_tile<T, E, 0, true>(a, tile, smem);
+        break;
+    }
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kBatchThreads) k_batched(const BatchSeg<T> *__restrict__ segs, int nseg,
+                                                           long long total, const T *f, T *u,
+                                                           unsigned long long *work, int *done, int *status,
+                                                           unsigned long long wait_ns)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    __shared__ long long s_item;
+    __shared__ int s_seg, s_abort;
+    while (true) {
+        __syncthreads(); // the previous item's shared-memory reads are finished
+        if (threadIdx.x == 0) {
+            s_item = (long long)atomicAdd(work, 1ull);
+            s_abort = 0;
+            if (s_item < total) {
+                int lo = 0, hi = nseg - 1;
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (segs[mid].first <= s_item) lo = mid;
+                    else hi = mid - 1;
+                }
+                s_seg = lo;
+                const int dep = segs[lo].dep;
+                if (dep >= 0 && !wait_count(&done[dep], segs[lo].need, wait_ns)) {
+                    s_abort = 1;
+                    atomicExch(status, (int)PSOLVE_ERR_TIMEOUT);
+                }
+            }
+        }
+        __syncthreads();
+        const long long item = s_item;
+        if (item >= total || s_abort) return;
+        const BatchSeg<T> &sg = segs[s_seg];
+        const long long tile = item - sg.first;
+        switch (sg.E) {
+        case 4: run_item<T, 4>(sg, tile, f, u, smraw); break;
+        case 8: run_item<T, 8>(sg, tile, f, u, smraw); break;
+        case 12: run_item<T, 12>(sg, tile, f, u, smraw); break;
+        case 16: run_item<T, 16>(sg, tile, f, u, smraw); break;
+        case 24: run_item<T, 24>(sg, tile, f, u, smraw); break;
+        default: break;
+        }
+        // Publish this tile: every thread's stores, then one release count.
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) atomicAdd(&done[s_seg], 1);
+    }
+}
+
+} // namespace
+
+// FP32 only; FP64 plans of unequal grids use one launch per pass and instance.
+template <typename T> const void *batched_kernel() { return reinterpret_cast<const void *>(&k_batched<T>); }
+template const void *batched_kernel<float>();
+
+template <typename T> cudaError_t batched_prepare(size_t smem)
+{
+    return cudaFuncSetAttribute(k_batched<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+template cudaError_t batched_prepare<float>(size_t);
+
+bool batched_supports_E(int E) { return E == 4 || E == 8 || E == 12 || E == 16 || E == 24; }
+
+} // namespace psolve

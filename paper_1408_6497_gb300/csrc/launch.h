@@ -50,6 +50,24 @@ size_t tma_smem_bytes(int L, int cfg);
 cudaError_t launch_strided_tma(const CUtensorMap &map, const TmaArgs &a, int L, int kind, int cfg,
                                unsigned grid, cudaStream_t s);
 
+// Persistent batched kernel: one segment per (pass, instance), pass-major.
+constexpr int kBatchThreads = 256;
+template <typename T> struct BatchSeg {
+    int kind;           // 0 zfwd, 1 yfwd, 2 xdiv, 3 yinv, 4 zinv
+    int E;              // points per thread of the pass's line
+    int dep;            // segment that must complete first, or -1
+    int need;           // completed tiles of `dep` to wait for (its tile count)
+    long long first;    // first item number of this segment
+    long long ntiles;
+    long long off;      // element offset of the instance in f and u
+    ZArgs<T> z;         // the member for this segment's pass is used;
+    SArgs<T> y;         // pointers to f/u are filled in by the kernel
+    XArgs<T> x;
+};
+template <typename T> const void *batched_kernel();
+template <typename T> cudaError_t batched_prepare(size_t smem);
+bool batched_supports_E(int E);
+
 // Twiddles e^{-2πi j/denom}, j < count, computed in FP64 and rounded to T.
 template <typename T>
 cudaError_t launch_roots(void *dst, int count, int denom, cudaStream_t s);

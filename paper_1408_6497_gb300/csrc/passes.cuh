@@ -68,26 +68,39 @@ template <typename T, int E, int LC> struct Bound {
     static constexpr int minb = (LC > 0 && sizeof(T) == 4) ? PSOLVE_CT_MINB : 1;
 };
 
+// Global loads of the pass data.  CG = true bypasses L1 (ld.global.cg): the
+// batched persistent kernel reads data that other blocks wrote earlier in
+// the same launch, which a stale L1 line could otherwise hide.
+template <bool CG, typename C> __device__ __forceinline__ C ld_data(const C *p)
+{
+    if constexpr (CG) return __ldcg(p);
+    else return *p;
+}
+
+// Every tile function below is called by all threads of a block (it
+// synchronises); threads beyond the tile's W·TL lanes are idle.  `smem` is
+// the block's dynamic shared memory: the line's twiddle table, then the
+// exchange buffer.
+
 // --------------------------------------------------------------- z forward
-template <typename T, int E, int LC>
-__global__ void __launch_bounds__(Bound<T, E, LC>::value, Bound<T, E, LC>::minb) k_zfwd(ZArgs<T> a)
+template <typename T, int E, int LC, bool CG = false>
+__device__ __forceinline__ void zfwd_tile(const ZArgs<T> &a, long long tile, unsigned char *smem)
 {
     using C = typename cplx_of<T>::type;
-    extern __shared__ __align__(16) unsigned char smraw[];
-    C *stw = reinterpret_cast<C *>(smraw);
+    C *stw = reinterpret_cast<C *>(smem);
     const int M = LC > 0 ? LC : a.M;
     C *sx = stw + M;
     const int TL = LC > 0 ? LC / E : a.pl.TL;
     const int tid = threadIdx.x;
     const int w = tid / TL, t = tid - w * TL;
-    const long long row = (long long)blockIdx.x * a.W + w;
+    const long long row = tile * a.W + w;
     const bool active = (w < a.W) && (row < a.rows);
     for (int i = tid; i < M; i += blockDim.x) stw[i] = a.tw[i];
     C v[E];
     if (active) {
         const C *src = reinterpret_cast<const C *>(a.in + row * (2 * M)) + t;
 #pragma unroll
-        for (int m = 0; m < E; ++m) v[m] = src[m * TL];
+        for (int m = 0; m < E; ++m) v[m] = ld_data<CG>(src + m * TL);
     } else {
 #pragma unroll
         for (int m = 0; m < E; ++m) v[m] = C{0, 0};
@@ -122,18 +135,17 @@ __global__ void __launch_bounds__(Bound<T, E, LC>::value, Bound<T, E, LC>::minb)
 }
 
 // --------------------------------------------------------------- z inverse
-template <typename T, int E, int LC>
-__global__ void __launch_bounds__(Bound<T, E, LC>::value, Bound<T, E, LC>::minb) k_zinv(ZArgs<T> a)
+template <typename T, int E, int LC, bool CG = false>
+__device__ __forceinline__ void zinv_tile(const ZArgs<T> &a, long long tile, unsigned char *smem)
 {
     using C = typename cplx_of<T>::type;
-    extern __shared__ __align__(16) unsigned char smraw[];
-    C *stw = reinterpret_cast<C *>(smraw);
+    C *stw = reinterpret_cast<C *>(smem);
     const int M = LC > 0 ? LC : a.M;
     C *sx = stw + M;
     const int TL = LC > 0 ? LC / E : a.pl.TL;
     const int tid = threadIdx.x;
     const int w = tid / TL, t = tid - w * TL;
-    const long long row = (long long)blockIdx.x * a.W + w;
+    const long long row = tile * a.W + w;
     const bool active = (w < a.W) && (row < a.rows);
     for (int i = tid; i < M; i += blockDim.x) stw[i] = a.tw[i];
     C v[E];
@@ -142,7 +154,7 @@ __global__ void __launch_bounds__(Bound<T, E, LC>::value, Bound<T, E, LC>::minb)
     if (active) {
         const C *src = reinterpret_cast<const C *>(a.in) + row * M + t;
 #pragma unroll
-        for (int m = 0; m < E; ++m) v[m] = src[m * TL];
+        for (int m = 0; m < E; ++m) v[m] = ld_data<CG>(src + m * TL);
 #pragma unroll
         for (int m = 0; m < E; ++m) sx[map(t + m * TL)] = v[m];
     }
@@ -175,29 +187,27 @@ __global__ void __launch_bounds__(Bound<T, E, LC>::value, Bound<T, E, LC>::minb)
 }
 
 // ------------------------------------------------------- strided c2c (y)
-template <typename T, int E, bool INV, int LC>
-__global__ void __launch_bounds__(Bound<T, E, LC>::value, Bound<T, E, LC>::minb) k_ypass(SArgs<T> a)
+template <typename T, int E, bool INV, int LC, bool CG = false>
+__device__ __forceinline__ void ypass_tile(const SArgs<T> &a, long long tile, unsigned char *smem)
 {
     using C = typename cplx_of<T>::type;
-    extern __shared__ __align__(16) unsigned char smraw[];
-    C *stw = reinterpret_cast<C *>(smraw);
+    C *stw = reinterpret_cast<C *>(smem);
     const int L = LC > 0 ? LC : a.pl.L;
     C *sx = stw + L;
     const int W = a.W, TL = LC > 0 ? LC / E : a.pl.TL;
     const int tid = threadIdx.x;
     const int w = tid % W, t = tid / W;
-    const long long tile = blockIdx.x;
     const int cb = (int)(tile % a.ncb);
     const long long plane = tile / a.ncb;
     const int col = cb * W + w;
-    const bool active = col < a.M;
+    const bool active = (col < a.M) && (t < TL);
     for (int i = tid; i < L; i += blockDim.x) stw[i] = a.tw[i];
     C *base = reinterpret_cast<C *>(a.data) + plane * a.sPlane + col + (long long)t * a.sL;
     const long long step = (long long)TL * a.sL;
     C v[E];
     if (active) {
 #pragma unroll
-        for (int m = 0; m < E; ++m) v[m] = base[m * step];
+        for (int m = 0; m < E; ++m) v[m] = ld_data<CG>(base + m * step);
     } else {
 #pragma unroll
         for (int m = 0; m < E; ++m) v[m] = C{0, 0};
@@ -219,7 +229,7 @@ __global__ void __launch_bounds__(Bound<T, E, LC>::value, Bound<T, E, LC>::minb)
 // Lines 2q and 2q+1 of the block hold rows ky and (ny - ky) mod ny; block
 // `pidx` takes pairs pidx·(W/2) .. pidx·(W/2) + W/2 - 1.  All threads of the
 // block must call it (it synchronises).
-template <typename T, int E, int LC>
+template <typename T, int E, int LC, bool CG = false>
 __device__ __forceinline__ void xpair_block(T *data, int nx_rt, int ny, int M, long long sInst, long long npairs,
                                             T coef, const LinePlan &pl, int W, int TL, long long pidx, int t,
                                             int w, const typename cplx_of<T>::type *stw,
@@ -234,7 +244,7 @@ __device__ __forceinline__ void xpair_block(T *data, int nx_rt, int ny, int M, l
     const int half = W >> 1;
     const int q = w >> 1, side = w & 1;
     const long long pair = pidx * half + q;
-    const bool active = (w < 2 * half) && (pair < npairs);
+    const bool active = (w < 2 * half) && (pair < npairs) && (t < TL);
     const int per = ny / 2 + 1;
     const long long b = active ? pair / per : 0;
     const int ky = active ? (int)(pair % per) : 0;
@@ -242,7 +252,7 @@ __device__ __forceinline__ void xpair_block(T *data, int nx_rt, int ny, int M, l
     C *base = reinterpret_cast<C *>(data) + b * sInst + (long long)row * M + (long long)t * sL;
     if (active) {
 #pragma unroll
-        for (int m = 0; m < E; ++m) v[m] = base[m * step];
+        for (int m = 0; m < E; ++m) v[m] = ld_data<CG>(base + m * step);
     } else {
 #pragma unroll
         for (int m = 0; m < E; ++m) v[m] = C{0, 0};
@@ -281,60 +291,88 @@ __device__ __forceinline__ void xpair_block(T *data, int nx_rt, int ny, int M, l
 }
 
 // ----------------------------------- x forward, spectral division, x inverse
-template <typename T, int E, int LC>
-__global__ void __launch_bounds__(Bound<T, E, LC>::value, Bound<T, E, LC>::minb) k_xfused(XArgs<T> a)
+// Tiles [0, main_tiles) are (instance, y, column block); the following ones
+// are groups of packed-column pairs.
+template <typename T, int E, int LC, bool CG = false>
+__device__ __forceinline__ void xfused_tile(const XArgs<T> &a, long long tile, unsigned char *smem)
 {
     using C = typename cplx_of<T>::type;
-    extern __shared__ __align__(16) unsigned char smraw[];
-    C *stw = reinterpret_cast<C *>(smraw);
+    C *stw = reinterpret_cast<C *>(smem);
     const int nx = LC > 0 ? LC : a.nx;
     C *sx = stw + nx;
     const int W = a.W, TL = LC > 0 ? LC / E : a.pl.TL, ny = a.ny, M = a.M;
     const int tid = threadIdx.x;
     const int w = tid % W, t = tid / W;
-    const long long tile = blockIdx.x;
     const long long sL = (long long)ny * M;
     const long long step = (long long)TL * sL;
     for (int i = tid; i < nx; i += blockDim.x) stw[i] = a.tw[i];
     const MapStrided map{W, w};
-    C v[E];
 
-    if (tile < a.main_tiles) {
-        const int cb = (int)(tile % a.ncb);
-        const long long rest = tile / a.ncb;
-        const int y = (int)(rest % ny);
-        const long long b = rest / ny;
-        const int col = cb * W + w;
-        const bool active = col < M;
-        C *base = reinterpret_cast<C *>(a.data) + b * a.sInst + (long long)y * M + col + (long long)t * sL;
-        if (active) {
-#pragma unroll
-            for (int m = 0; m < E; ++m) v[m] = base[m * step];
-        } else {
-#pragma unroll
-            for (int m = 0; m < E; ++m) v[m] = C{0, 0};
-        }
-        __syncthreads();
-        line_fft_any<false, LC>(v, t, a.pl, stw, sx, map, active);
-        const int ky = kvec_dev(y, ny);
-        const int kyz = ky * ky + col * col;
-#pragma unroll
-        for (int m = 0; m < E; ++m) {
-            const int kx = kvec_dev(t + m * TL, nx);
-            const int k2 = kx * kx + kyz;
-            const T d = (k2 == 0) ? (T)0 : a.coef / (T)k2;
-            v[m] = cscale(v[m], d);
-        }
-        line_fft_any<true, LC>(v, t, a.pl, stw, sx, map, active);
-        if (active && col != 0) {
-#pragma unroll
-            for (int m = 0; m < E; ++m) base[m * step] = v[m];
-        }
+    if (tile >= a.main_tiles) {
+        xpair_block<T, E, LC, CG>(a.data, nx, ny, M, a.sInst, a.npairs, a.coef, a.pl, W, TL, tile - a.main_tiles,
+                                  t, w, stw, sx);
         return;
     }
+    C v[E];
+    const int cb = (int)(tile % a.ncb);
+    const long long rest = tile / a.ncb;
+    const int y = (int)(rest % ny);
+    const long long b = rest / ny;
+    const int col = cb * W + w;
+    const bool active = (col < M) && (t < TL);
+    C *base = reinterpret_cast<C *>(a.data) + b * a.sInst + (long long)y * M + col + (long long)t * sL;
+    if (active) {
+#pragma unroll
+        for (int m = 0; m < E; ++m) v[m] = ld_data<CG>(base + m * step);
+    } else {
+#pragma unroll
+        for (int m = 0; m < E; ++m) v[m] = C{0, 0};
+    }
+    __syncthreads();
+    line_fft_any<false, LC>(v, t, a.pl, stw, sx, map, active);
+    const int ky = kvec_dev(y, ny);
+    const int kyz = ky * ky + col * col;
+#pragma unroll
+    for (int m = 0; m < E; ++m) {
+        const int kx = kvec_dev(t + m * TL, nx);
+        const int k2 = kx * kx + kyz;
+        const T d = (k2 == 0) ? (T)0 : a.coef / (T)k2;
+        v[m] = cscale(v[m], d);
+    }
+    line_fft_any<true, LC>(v, t, a.pl, stw, sx, map, active);
+    if (active && col != 0) {
+#pragma unroll
+        for (int m = 0; m < E; ++m) base[m * step] = v[m];
+    }
+}
 
-    xpair_block<T, E, LC>(a.data, nx, ny, M, a.sInst, a.npairs, a.coef, a.pl, W, TL, tile - a.main_tiles, t,
-                          w, stw, sx);
+// ------------------------------------------------------- one-pass kernels
+template <typename T, int E, int LC>
+__global__ void __launch_bounds__(Bound<T, E, LC>::value, Bound<T, E, LC>::minb) k_zfwd(ZArgs<T> a)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    zfwd_tile<T, E, LC>(a, blockIdx.x, smraw);
+}
+
+template <typename T, int E, int LC>
+__global__ void __launch_bounds__(Bound<T, E, LC>::value, Bound<T, E, LC>::minb) k_zinv(ZArgs<T> a)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    zinv_tile<T, E, LC>(a, blockIdx.x, smraw);
+}
+
+template <typename T, int E, bool INV, int LC>
+__global__ void __launch_bounds__(Bound<T, E, LC>::value, Bound<T, E, LC>::minb) k_ypass(SArgs<T> a)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    ypass_tile<T, E, INV, LC>(a, blockIdx.x, smraw);
+}
+
+template <typename T, int E, int LC>
+__global__ void __launch_bounds__(Bound<T, E, LC>::value, Bound<T, E, LC>::minb) k_xfused(XArgs<T> a)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    xfused_tile<T, E, LC>(a, blockIdx.x, smraw);
 }
 
 } // namespace psolve
