@@ -114,6 +114,17 @@ psolve_status psolve_debug_kvec(const psolve_plan *plan, int b, int *kxyz_out);
 psolve_status psolve_error_norms(const void *a, const void *ref, size_t n, int dtype,
                                  double *out4, void *stream);
 
+/* Autotune the plan in place: time candidate tile widths, TMA tile
+ * configurations and (for the persistent batched launch) radix orders of
+ * each pass on a scratch copy of one instance, keep the fastest, and store
+ * the choices in a per-GPU cache file ($PSOLVE_TUNE_CACHE, else
+ * $HOME/.cache/psolve/tune-v1.txt) that later psolve_plan_create /
+ * psolve_plan_create_many calls read.  This is the setup-time tuning that
+ * §3 and Table 1 amortise over many solves.  Synchronises `stream`,
+ * allocates and frees one instance of scratch, and must not run while a
+ * solve of this plan is in flight.  Results are unchanged up to rounding. */
+psolve_status psolve_autotune(psolve_plan *plan, void *stream);
+
 /* Per-pass timing with CUDA events recorded on the solve's own stream.
  * After psolve_set_profiling(plan, 1), every psolve_execute/psolve_adjoint
  * records an event before the first pass and after each pass; the kernels

@@ -24,7 +24,7 @@ STATUS = {0: "PSOLVE_OK", 1: "PSOLVE_ERR_INVALID_ARG", 2: "PSOLVE_ERR_UNSUPPORTE
 EXPORTS = ("psolve_plan_create", "psolve_plan_create_many", "psolve_execute", "psolve_adjoint",
            "psolve_execute_host", "psolve_destroy", "psolve_instance_offset",
            "psolve_total_elements", "psolve_get_status", "psolve_debug_kvec",
-           "psolve_error_norms", "psolve_set_profiling", "psolve_pass_times", "psolve_pass_name",
+           "psolve_error_norms", "psolve_autotune", "psolve_set_profiling", "psolve_pass_times", "psolve_pass_name",
            "psolve_launches_per_solve", "psolve_debug_set_wait", "psolve_execute_noalloc", "psolve_status_string",
            "psolve_last_error", "psolve_version")
 
@@ -65,6 +65,7 @@ def load(path: str | None = None):
         lib.psolve_get_status.argtypes = [vp, vp]
         lib.psolve_debug_kvec.argtypes = [vp, i, ip]
         lib.psolve_error_norms.argtypes = [vp, vp, sz, i, ctypes.POINTER(ctypes.c_double), vp]
+        lib.psolve_autotune.argtypes = [vp, vp]
         lib.psolve_set_profiling.argtypes = [vp, i]
         lib.psolve_pass_times.argtypes = [vp, ctypes.POINTER(ctypes.c_double), i, ip, ip]
         lib.psolve_pass_name.argtypes = [vp, i]

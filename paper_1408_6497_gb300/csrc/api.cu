@@ -18,6 +18,9 @@
 #include <string>
 #include <vector>
 
+#include <sys/stat.h>
+#include <unistd.h>
+
 using namespace psolve;
 
 namespace {
@@ -46,6 +49,9 @@ struct Group {
     LinePlan pz, py, px;
     size_t tw_z, tw_y, tw_x, post; // complex-element offsets into the table buffer
     int Wz, Wy, Wx;
+    int cfg_y, cfg_x;    // TMA configuration of the y / x pass (-1: per-tile kernel)
+    int bWz, bWy, bWx;   // tile widths inside the persistent batched launch (0: default)
+    int order;           // radix order of the run-time stage plans (see make_line_plan)
 };
 
 bool factor23(int n, int &a, int &b)
@@ -64,8 +70,10 @@ bool size_ok(int n)
 }
 
 // Stage plan of an L-point line: radix-3 stages for the factors of 3, then
-// the largest power-of-two radices (<= 16) that divide E.
-bool make_line_plan(int L, LinePlan &p)
+// the largest power-of-two radices (<= 16) that divide E (order 0).  Order 1
+// runs the same radices in reverse, order 2 puts the radix-3 stages last;
+// any order is a valid Stockham factorisation, and the autotuner times them.
+bool make_line_plan(int L, LinePlan &p, int order = 0)
 {
     int a, b;
     if (!factor23(L, a, b) || L < 2) return false;
@@ -85,6 +93,8 @@ bool make_line_plan(int L, LinePlan &p)
         rem /= r;
     }
     if ((int)rad.size() > kMaxStages) return false;
+    if (order == 1) std::reverse(rad.begin(), rad.end());
+    if (order == 2) std::rotate(rad.begin(), rad.begin() + b, rad.end());
     p.nst = (int)rad.size();
     int ns = 1;
     for (int s = 0; s < p.nst; ++s) {
@@ -190,6 +200,7 @@ void choose_tiles(Group &g, int dtype)
 
 struct psolve_plan {
     unsigned magic;
+    bool uniform; // psolve_plan_create (equal grids back to back)
     int dtype;
     int device;
     int num_sms;
@@ -291,6 +302,131 @@ void release(psolve_plan *p)
     delete p;
 }
 
+// Whether the persistent TMA pass applies to lines of length L over M columns.
+int tma_variant(int setting, int L) { return setting >= 0 ? setting : (tma_columns(L, 1) >= 8 ? 1 : 0); }
+
+bool tma_fits(const psolve_plan *p, int L, int M, int narrow)
+{
+    return p->use_tma && p->dtype != PSOLVE_F64 && tma_supported(L) && (M % 2) == 0 &&
+           M >= tma_columns(L, narrow);
+}
+
+// ------------------------------------------------------------ tuning cache
+// One line per tuned choice:
+//   <gpu>|<dtype>|<path>|<axis>|<L>|<M> <W> <cfg> <order>
+// path "pass" = the one-pass-per-launch solve, "batch" = the persistent
+// batched launch; axis z (rows of M), y or x (lines of L over M columns).
+std::string tune_cache_path()
+{
+    if (const char *e = std::getenv("PSOLVE_TUNE_CACHE")) return e;
+    if (const char *h = std::getenv("HOME")) return std::string(h) + "/.cache/psolve/tune-v1.txt";
+    return "";
+}
+
+std::string gpu_key(int device)
+{
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) return "unknown";
+    std::string n = prop.name;
+    for (auto &c : n)
+        if (c == ' ' || c == '|') c = '_';
+    return n;
+}
+
+std::string tune_key(const psolve_plan *p, const char *path, char axis, int L, int M)
+{
+    return gpu_key(p->device) + "|" + std::to_string(p->dtype) + "|" + path + "|" + axis + "|" +
+           std::to_string(L) + "|" + std::to_string(M);
+}
+
+struct TuneChoice {
+    int W, cfg, order;
+};
+
+std::map<std::string, TuneChoice> read_tune_cache()
+{
+    std::map<std::string, TuneChoice> m;
+    const std::string path = tune_cache_path();
+    if (path.empty()) return m;
+    FILE *fh = std::fopen(path.c_str(), "r");
+    if (!fh) return m;
+    char key[512];
+    int W, cfg, order;
+    while (std::fscanf(fh, "%511s %d %d %d", key, &W, &cfg, &order) == 4) m[key] = TuneChoice{W, cfg, order};
+    std::fclose(fh);
+    return m;
+}
+
+void write_tune_cache(const std::map<std::string, TuneChoice> &m)
+{
+    const std::string path = tune_cache_path();
+    if (path.empty()) return;
+    const size_t slash = path.rfind('/');
+    if (slash != std::string::npos) {
+        std::string dir = path.substr(0, slash);
+        for (size_t i = 1; i <= dir.size(); ++i)
+            if (i == dir.size() || dir[i] == '/') mkdir(dir.substr(0, i).c_str(), 0755);
+    }
+    const std::string tmp = path + ".tmp" + std::to_string((long)getpid());
+    FILE *fh = std::fopen(tmp.c_str(), "w");
+    if (!fh) return;
+    for (const auto &kv : m) std::fprintf(fh, "%s %d %d %d\n", kv.first.c_str(), kv.second.W, kv.second.cfg, kv.second.order);
+    std::fclose(fh);
+    std::rename(tmp.c_str(), path.c_str());
+}
+
+// Apply cached choices that are still valid for this plan.
+void apply_tuning_cache(psolve_plan *p)
+{
+    const auto m = read_tune_cache();
+    if (m.empty()) return;
+    const bool fp64 = p->dtype == PSOLVE_F64;
+    const bool uniform = p->uniform;
+    for (auto &g : p->groups) {
+        const char *path = uniform ? "pass" : "batch";
+        auto it = m.find(tune_key(p, path, 'z', g.M, g.M));
+        if (it != m.end() && it->second.W >= 1) {
+            const int keep = g.Wz;
+            if (uniform) g.Wz = it->second.W; else g.bWz = it->second.W;
+            if (uniform && (g.Wz * g.pz.TL > max_threads(fp64, g.pz.E) || z_smem(g, p->dtype) > kSmemCap)) g.Wz = keep;
+            LinePlan pl;
+            if (!uniform && make_line_plan(g.M, pl, it->second.order)) g.pz = pl;
+        }
+        it = m.find(tune_key(p, path, 'y', g.ny, g.M));
+        if (it != m.end()) {
+            const TuneChoice c = it->second;
+            if (uniform) {
+                if (c.cfg >= 0 && tma_fits(p, g.ny, g.M, c.cfg)) g.cfg_y = c.cfg;
+                else if (c.cfg < 0 && c.W >= 1 && c.W <= g.M && c.W * g.py.TL <= max_threads(fp64, g.py.E) &&
+                         s_smem(g.ny, c.W, p->dtype) <= kSmemCap) {
+                    g.cfg_y = -1;
+                    g.Wy = c.W;
+                }
+            } else {
+                g.bWy = c.W;
+                LinePlan pl;
+                if (make_line_plan(g.ny, pl, c.order)) g.py = pl;
+            }
+        }
+        it = m.find(tune_key(p, path, 'x', g.nx, g.M));
+        if (it != m.end()) {
+            const TuneChoice c = it->second;
+            if (uniform) {
+                if (c.cfg >= 0 && tma_fits(p, g.nx, g.M, c.cfg)) g.cfg_x = c.cfg;
+                else if (c.cfg < 0 && c.W >= 2 && c.W * g.px.TL <= max_threads(fp64, g.px.E) &&
+                         s_smem(g.nx, c.W, p->dtype) <= kSmemCap) {
+                    g.cfg_x = -1;
+                    g.Wx = c.W;
+                }
+            } else {
+                g.bWx = c.W;
+                LinePlan pl;
+                if (make_line_plan(g.nx, pl, c.order)) g.px = pl;
+            }
+        }
+    }
+}
+
 // Segments of the persistent batched launch: pass-major, one per (pass,
 // instance), each with a tile width that fits kBatchThreads threads.
 template <typename T> psolve_status setup_batched(psolve_plan *p)
@@ -313,7 +449,7 @@ template <typename T> psolve_status setup_batched(psolve_plan *p)
             sg.off = (long long)g.off0;
             const int M = g.M;
             if (pass == 0 || pass == 4) {
-                int W = std::max(1, NT / g.pz.TL);
+                int W = g.bWz > 0 ? std::min(g.bWz, std::max(1, NT / g.pz.TL)) : std::max(1, NT / g.pz.TL);
                 const int LP = M + (M >> 4) + 1;
                 while (W > 1 && (size_t)(M + (size_t)W * LP) * cs > kSmemCap) W /= 2;
                 sg.E = g.pz.E;
@@ -328,6 +464,7 @@ template <typename T> psolve_status setup_batched(psolve_plan *p)
                 smem = std::max(smem, (size_t)(M + (size_t)W * LP) * cs);
             } else if (pass == 1 || pass == 3) {
                 int W = std::min(M, std::max(1, NT / g.py.TL));
+                if (g.bWy > 0) W = std::min(W, g.bWy);
                 while (W > 1 && s_smem(g.ny, W, p->dtype) > kSmemCap) W /= 2;
                 sg.E = g.py.E;
                 sg.y.nplanes = g.nx;
@@ -342,6 +479,7 @@ template <typename T> psolve_status setup_batched(psolve_plan *p)
                 smem = std::max(smem, s_smem(g.ny, W, p->dtype));
             } else {
                 int W = std::max(2, std::min(std::max(2, M), NT / g.px.TL));
+                if (g.bWx > 0) W = std::max(2, std::min(W, g.bWx));
                 while (W > 2 && s_smem(g.nx, W, p->dtype) > kSmemCap) W /= 2;
                 if (W * g.px.TL > NT) return fail(PSOLVE_ERR_UNSUPPORTED_SIZE, "x line too long for a batch tile");
                 sg.E = g.px.E;
@@ -400,6 +538,7 @@ psolve_status build_plan(const std::vector<int> &nx, const std::vector<int> &ny,
     const size_t align = 32;
     std::unique_ptr<psolve_plan> p(new psolve_plan());
     p->magic = kMagic;
+    p->uniform = uniform;
     p->dtype = dtype;
     p->batch = batch;
     p->tables = nullptr;
@@ -479,6 +618,13 @@ psolve_status build_plan(const std::vector<int> &nx, const std::vector<int> &ny,
             p->tma_narrow_x = nx_ < 0 || nx_ > 2 ? 0 : nx_;
         }
     }
+    for (auto &g : p->groups) {
+        g.cfg_y = tma_fits(p.get(), g.ny, g.M, tma_variant(p->tma_narrow_y, g.ny))
+                      ? tma_variant(p->tma_narrow_y, g.ny) : -1;
+        g.cfg_x = tma_fits(p.get(), g.nx, g.M, tma_variant(p->tma_narrow_x, g.nx))
+                      ? tma_variant(p->tma_narrow_x, g.nx) : -1;
+    }
+    apply_tuning_cache(p.get());
     e = cudaMalloc(&p->tables, tcount * csize(dtype));
     if (e != cudaSuccess) {
         p->tables = nullptr;
@@ -557,14 +703,6 @@ bool encode_map(CUtensorMap *m, void *base, uint64_t d0, uint64_t d1, uint64_t d
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-// Whether the persistent TMA pass applies to lines of length L over M columns.
-int tma_variant(int setting, int L) { return setting >= 0 ? setting : (tma_columns(L, 1) >= 8 ? 1 : 0); }
-
-bool tma_fits(const psolve_plan *p, int L, int M, int narrow)
-{
-    return p->use_tma && p->dtype != PSOLVE_F64 && tma_supported(L) && (M % 2) == 0 &&
-           M >= tma_columns(L, narrow);
-}
 
 template <typename T>
 psolve_status run_tma_pass(const psolve_plan *p, const Group &g, T *ui, int kind, cudaStream_t s)
@@ -573,7 +711,7 @@ psolve_status run_tma_pass(const psolve_plan *p, const Group &g, T *ui, int kind
         return fail(PSOLVE_ERR_INTERNAL, "TMA pass is FP32 only");
     } else {
         const int L = kind == 2 ? g.nx : g.ny;
-        const int narrow = tma_variant(kind == 2 ? p->tma_narrow_x : p->tma_narrow_y, L);
+        const int narrow = kind == 2 ? g.cfg_x : g.cfg_y;
         const int W = tma_columns(L, narrow);
         const int boxr = L < 256 ? L : 256;
         CUtensorMap map;
@@ -605,61 +743,55 @@ psolve_status run_tma_pass(const psolve_plan *p, const Group &g, T *ui, int kind
     }
 }
 
+// Enqueue pass `kind` (0 zfwd, 1 yfwd, 2 x with division, 3 yinv, 4 zinv)
+// of a group with its current tile choices.
 template <typename T>
-psolve_status run_group(const psolve_plan *p, const Group &g, const T *f, T *u, cudaStream_t s,
-                        const std::vector<cudaEvent_t> *ev)
+psolve_status launch_pass(const psolve_plan *p, const Group &g, int kind, const T *fi, T *ui, cudaStream_t s,
+                          bool force_runtime = false)
 {
-    auto mark = [&](int i) {
-        if (ev) cudaEventRecord((*ev)[i], s);
-    };
     using C = typename cplx_of<T>::type;
     const C *tab = reinterpret_cast<const C *>(p->tables);
-    const T *fi = f + g.off0;
-    T *ui = u + g.off0;
     const int dtype = p->dtype;
     cudaError_t e;
-
-    ZArgs<T> z{};
-    z.in = fi;
-    z.out = ui;
-    z.rows = (long long)g.count * g.nx * g.ny;
-    z.nz = g.nz;
-    z.M = g.M;
-    z.W = g.Wz;
-    z.pl = g.pz;
-    z.tw = tab + g.tw_z;
-    z.post = tab + g.post;
-    const unsigned zgrid = ceil_div(z.rows, g.Wz);
-    const unsigned zblock = (unsigned)(g.Wz * g.pz.TL);
-    mark(0);
-    e = launch_zfwd<T>(z, zgrid, zblock, z_smem(g, dtype), s);
-    if (e != cudaSuccess) return cuda_fail(e, "z forward pass");
-    mark(1);
-
-    SArgs<T> y{};
-    y.data = ui;
-    y.nplanes = (long long)g.count * g.nx;
-    y.sPlane = (long long)g.ny * g.M;
-    y.sL = g.M;
-    y.M = g.M;
-    y.W = g.Wy;
-    y.ncb = (g.M + g.Wy - 1) / g.Wy;
-    y.pl = g.py;
-    y.tw = tab + g.tw_y;
-    const unsigned ygrid = (unsigned)(y.nplanes * y.ncb);
-    const unsigned yblock = (unsigned)(g.Wy * g.py.TL);
-    const size_t ysm = s_smem(g.ny, g.Wy, dtype);
-    const bool tma_y = tma_fits(p, g.ny, g.M, tma_variant(p->tma_narrow_y, g.ny));
-    const bool tma_x = tma_fits(p, g.nx, g.M, tma_variant(p->tma_narrow_x, g.nx));
-    if (tma_y) {
-        psolve_status st = run_tma_pass<T>(p, g, ui, 0, s);
-        if (st != PSOLVE_OK) return st;
-    } else {
-        e = launch_ypass<T>(y, false, ygrid, yblock, ysm, s);
-        if (e != cudaSuccess) return cuda_fail(e, "y forward pass");
+    if (kind == 0 || kind == 4) {
+        ZArgs<T> z{};
+        z.in = kind == 0 ? fi : ui;
+        z.out = ui;
+        z.rows = (long long)g.count * g.nx * g.ny;
+        z.nz = g.nz;
+        z.M = g.M;
+        z.W = g.Wz;
+        z.pl = g.pz;
+        z.tw = tab + g.tw_z;
+        z.post = tab + g.post;
+        z.force_runtime = force_runtime;
+        const unsigned grid = ceil_div(z.rows, g.Wz);
+        const unsigned block = (unsigned)(g.Wz * g.pz.TL);
+        e = kind == 0 ? launch_zfwd<T>(z, grid, block, z_smem(g, dtype), s)
+                      : launch_zinv<T>(z, grid, block, z_smem(g, dtype), s);
+        if (e != cudaSuccess) return cuda_fail(e, kind == 0 ? "z forward pass" : "z inverse pass");
+        return PSOLVE_OK;
     }
-    mark(2);
-
+    if (kind == 1 || kind == 3) {
+        if (g.cfg_y >= 0) return run_tma_pass<T>(p, g, ui, kind == 1 ? 0 : 1, s);
+        SArgs<T> y{};
+        y.data = ui;
+        y.nplanes = (long long)g.count * g.nx;
+        y.sPlane = (long long)g.ny * g.M;
+        y.sL = g.M;
+        y.M = g.M;
+        y.W = g.Wy;
+        y.ncb = (g.M + g.Wy - 1) / g.Wy;
+        y.pl = g.py;
+        y.tw = tab + g.tw_y;
+        y.force_runtime = force_runtime;
+        const unsigned grid = (unsigned)(y.nplanes * y.ncb);
+        const unsigned block = (unsigned)(g.Wy * g.py.TL);
+        e = launch_ypass<T>(y, kind == 3, grid, block, s_smem(g.ny, g.Wy, dtype), s);
+        if (e != cudaSuccess) return cuda_fail(e, kind == 1 ? "y forward pass" : "y inverse pass");
+        return PSOLVE_OK;
+    }
+    if (g.cfg_x >= 0) return run_tma_pass<T>(p, g, ui, 2, s);
     XArgs<T> x{};
     x.data = ui;
     x.batch = g.count;
@@ -673,34 +805,27 @@ psolve_status run_group(const psolve_plan *p, const Group &g, const T *f, T *u, 
     x.npairs = (long long)g.count * (g.ny / 2 + 1);
     x.pl = g.px;
     x.tw = tab + g.tw_x;
-    const double N = (double)g.nx * g.ny * g.nz;
-    x.coef = (T)(1.0 / (4.0 * M_PI * M_PI * N));
-    const unsigned xgrid = (unsigned)(x.main_tiles + (x.npairs + g.Wx / 2 - 1) / (g.Wx / 2));
-    const unsigned xblock = (unsigned)(g.Wx * g.px.TL);
-    if (tma_x) {
-        psolve_status st = run_tma_pass<T>(p, g, ui, 2, s);
-        if (st != PSOLVE_OK) return st;
-    } else {
-        e = launch_xfused<T>(x, xgrid, xblock, s_smem(g.nx, g.Wx, dtype), s);
-        if (e != cudaSuccess) return cuda_fail(e, "x pass with spectral division");
-    }
-    mark(3);
+    x.coef = (T)(1.0 / (4.0 * M_PI * M_PI * ((double)g.nx * g.ny * g.nz)));
+    x.force_runtime = force_runtime;
+    const unsigned grid = (unsigned)(x.main_tiles + (x.npairs + g.Wx / 2 - 1) / (g.Wx / 2));
+    const unsigned block = (unsigned)(g.Wx * g.px.TL);
+    e = launch_xfused<T>(x, grid, block, s_smem(g.nx, g.Wx, dtype), s);
+    if (e != cudaSuccess) return cuda_fail(e, "x pass with spectral division");
+    return PSOLVE_OK;
+}
 
-    if (tma_y) {
-        psolve_status st = run_tma_pass<T>(p, g, ui, 1, s);
+template <typename T>
+psolve_status run_group(const psolve_plan *p, const Group &g, const T *f, T *u, cudaStream_t s,
+                        const std::vector<cudaEvent_t> *ev)
+{
+    const T *fi = f + g.off0;
+    T *ui = u + g.off0;
+    if (ev) cudaEventRecord((*ev)[0], s);
+    for (int kind = 0; kind < kPasses; ++kind) {
+        psolve_status st = launch_pass<T>(p, g, kind, fi, ui, s);
         if (st != PSOLVE_OK) return st;
-    } else {
-        e = launch_ypass<T>(y, true, ygrid, yblock, ysm, s);
-        if (e != cudaSuccess) return cuda_fail(e, "y inverse pass");
+        if (ev) cudaEventRecord((*ev)[kind + 1], s);
     }
-    mark(4);
-
-    ZArgs<T> zi = z;
-    zi.in = ui;
-    zi.out = ui;
-    e = launch_zinv<T>(zi, zgrid, zblock, z_smem(g, dtype), s);
-    if (e != cudaSuccess) return cuda_fail(e, "z inverse pass");
-    mark(5);
     return PSOLVE_OK;
 }
 
@@ -789,6 +914,145 @@ psolve_status solve(psolve_plan *p, const void *f, void *u, void *stream)
                  : run_group<float>(p, g, (const float *)f, (float *)u, s, ev);
         if (st != PSOLVE_OK) return st;
     }
+    return PSOLVE_OK;
+}
+
+
+// ------------------------------------------------------------- autotuner
+// Times candidate tile widths, TMA configurations and radix orders of each
+// pass on a scratch instance and keeps the fastest (the analogue of the FFT
+// library "MEASURE" planning the paper's setup phase pays once, §3 Table 1).
+template <typename T> psolve_status autotune_impl(psolve_plan *p, cudaStream_t s)
+{
+    const bool fp64 = p->dtype == PSOLVE_F64;
+    size_t maxN = 0;
+    for (const auto &g : p->groups) maxN = std::max(maxN, (size_t)g.nx * g.ny * g.nz);
+    T *buf = nullptr;
+    if (cudaMalloc(&buf, maxN * sizeof(T)) != cudaSuccess) return fail(PSOLVE_ERR_OOM, "autotune scratch");
+    cudaMemsetAsync(buf, 0x3c, maxN * sizeof(T), s);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const float inf = 1e30f;
+    auto timed = [&](const Group &gt, int kind, bool rt) -> float {
+        if (launch_pass<T>(p, gt, kind, buf, buf, s, rt) != PSOLVE_OK) return inf;
+        const int reps = 3;
+        cudaEventRecord(e0, s);
+        for (int r = 0; r < reps; ++r)
+            if (launch_pass<T>(p, gt, kind, buf, buf, s, rt) != PSOLVE_OK) return inf;
+        cudaEventRecord(e1, s);
+        if (cudaEventSynchronize(e1) != cudaSuccess) return inf;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        return ms / reps;
+    };
+    auto cache = read_tune_cache();
+    const int wlist[] = {1, 2, 4, 8, 16, 32, 64};
+    for (auto &g : p->groups) {
+        Group gt = g;
+        gt.count = 1;
+        gt.off0 = 0;
+        if (!p->batched) {
+            // z rows per block
+            float best = inf;
+            int bw = g.Wz;
+            for (int W : wlist) {
+                gt.Wz = W;
+                if (W * gt.pz.TL > max_threads(fp64, gt.pz.E) || z_smem(gt, p->dtype) > kSmemCap) continue;
+                const float t = timed(gt, 0, false) + timed(gt, 4, false);
+                if (t < best) { best = t; bw = W; }
+            }
+            g.Wz = gt.Wz = bw;
+            cache[tune_key(p, "pass", 'z', g.M, g.M)] = TuneChoice{bw, -1, 0};
+            // y and x: TMA configurations and per-tile widths
+            for (int axis = 0; axis < 2; ++axis) {
+                const int L = axis == 0 ? g.ny : g.nx;
+                const int kind = axis == 0 ? 1 : 2;
+                const LinePlan &pl = axis == 0 ? g.py : g.px;
+                float bt = inf;
+                int bcfg = -1, bW = axis == 0 ? g.Wy : g.Wx;
+                for (int cfg = 0; cfg < 3 && !fp64; ++cfg) {
+                    if (!tma_fits(p, L, g.M, cfg)) continue;
+                    if (axis == 0) gt.cfg_y = cfg; else gt.cfg_x = cfg;
+                    const float t = timed(gt, kind, false);
+                    if (t < bt) { bt = t; bcfg = cfg; }
+                }
+                if (axis == 0) gt.cfg_y = -1; else gt.cfg_x = -1;
+                for (int W : wlist) {
+                    if (W < (axis == 0 ? 1 : 2) || (axis == 0 && W > g.M) || W * pl.TL > max_threads(fp64, pl.E) ||
+                        s_smem(L, W, p->dtype) > kSmemCap)
+                        continue;
+                    if (axis == 0) gt.Wy = W; else gt.Wx = W;
+                    const float t = timed(gt, kind, false);
+                    if (t < bt) { bt = t; bcfg = -1; bW = W; }
+                }
+                if (axis == 0) { g.cfg_y = gt.cfg_y = bcfg; g.Wy = gt.Wy = bW; }
+                else { g.cfg_x = gt.cfg_x = bcfg; g.Wx = gt.Wx = bW; }
+                cache[tune_key(p, "pass", axis == 0 ? 'y' : 'x', L, g.M)] = TuneChoice{bW, bcfg, 0};
+            }
+        } else {
+            // Inside the persistent launch: tile widths that fit its blocks and
+            // the radix order of each line's run-time plan.
+            gt.cfg_y = gt.cfg_x = -1;
+            for (int axis = 0; axis < 3; ++axis) {
+                const int L = axis == 0 ? g.M : (axis == 1 ? g.ny : g.nx);
+                const char key = axis == 0 ? 'z' : (axis == 1 ? 'y' : 'x');
+                float bt = inf;
+                int bW = 0, bo = 0;
+                for (int order = 0; order < 3; ++order) {
+                    LinePlan pl;
+                    if (!make_line_plan(L, pl, order)) continue;
+                    const int wmax = std::max(axis == 2 ? 2 : 1, kBatchThreads / pl.TL);
+                    for (int d = 1; d <= 4; d *= 2) {
+                        int W = std::max(axis == 2 ? 2 : 1, wmax / d);
+                        if (axis != 0) W = std::min(W, std::max(axis == 2 ? 2 : 1, g.M));
+                        float t;
+                        if (axis == 0) {
+                            gt.pz = pl;
+                            gt.Wz = W;
+                            if (z_smem(gt, p->dtype) > kSmemCap) continue;
+                            t = timed(gt, 0, true) + timed(gt, 4, true);
+                        } else if (axis == 1) {
+                            gt.py = pl;
+                            gt.Wy = W;
+                            if (s_smem(L, W, p->dtype) > kSmemCap) continue;
+                            t = timed(gt, 1, true);
+                        } else {
+                            gt.px = pl;
+                            gt.Wx = W;
+                            if (s_smem(L, W, p->dtype) > kSmemCap) continue;
+                            t = timed(gt, 2, true);
+                        }
+                        if (t < bt) { bt = t; bW = W; bo = order; }
+                    }
+                }
+                LinePlan best;
+                make_line_plan(L, best, bo);
+                if (axis == 0) { g.pz = gt.pz = best; g.bWz = bW; gt.Wz = bW; }
+                else if (axis == 1) { g.py = gt.py = best; g.bWy = bW; gt.Wy = bW; }
+                else { g.px = gt.px = best; g.bWx = bW; gt.Wx = bW; }
+                cache[tune_key(p, "batch", key, L, g.M)] = TuneChoice{bW, -1, bo};
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(buf);
+    if (p->batched) {
+        // Rebuild the segment table and its graph with the new choices.
+        if (p->gexec) cudaGraphExecDestroy(p->gexec);
+        if (p->graph) cudaGraphDestroy(p->graph);
+        if (p->segs_dev) cudaFree(p->segs_dev);
+        if (p->counters) cudaFree(p->counters);
+        p->gexec = nullptr;
+        p->graph = nullptr;
+        p->segs_dev = nullptr;
+        p->counters = nullptr;
+        p->batched = false;
+        psolve_status st = setup_batched<float>(p);
+        if (st != PSOLVE_OK) return st;
+    }
+    write_tune_cache(cache);
     return PSOLVE_OK;
 }
 
@@ -951,6 +1215,17 @@ psolve_status psolve_error_norms(const void *a, const void *ref, size_t n, int d
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(e, "error norms");
     return PSOLVE_OK;
+}
+
+psolve_status psolve_autotune(psolve_plan *plan, void *stream)
+{
+    if (!plan_ok(plan)) return fail(PSOLVE_ERR_INVALID_ARG, "invalid or destroyed plan");
+    DeviceGuard dg(plan->device);
+    if (dg.err != cudaSuccess) return cuda_fail(dg.err, "select device");
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "synchronise stream");
+    return plan->dtype == PSOLVE_F64 ? autotune_impl<double>(plan, s) : autotune_impl<float>(plan, s);
 }
 
 psolve_status psolve_set_profiling(psolve_plan *plan, int enable)

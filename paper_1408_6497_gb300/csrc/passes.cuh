@@ -35,6 +35,7 @@ template <typename T> struct ZArgs {
     LinePlan pl;      // L = M
     const C *tw;      // e^{-2πi j/M}, j < M
     const C *post;    // e^{-2πi k/nz}, k < M
+    int force_runtime; // host dispatch: 1 = run-time stage plan even for hot lengths
 };
 
 template <typename T> struct SArgs {
@@ -46,6 +47,7 @@ template <typename T> struct SArgs {
     int M, W, ncb;    // columns per row, columns per tile, tiles per plane
     LinePlan pl;
     const C *tw;
+    int force_runtime;
 };
 
 template <typename T> struct XArgs {
@@ -59,6 +61,7 @@ template <typename T> struct XArgs {
     LinePlan pl;         // L = nx
     const C *tw;
     T coef;              // 1 / (4π² N), N = nx·ny·nz
+    int force_runtime;
 };
 
 // Launch bound per instantiation: the host mirrors this in max_threads().

@@ -19,7 +19,7 @@ template <typename T, bool INV>
 static cudaError_t dispatch(const SArgs<T> &a, unsigned grid, unsigned block, size_t smem, cudaStream_t s)
 {
     // Compile-time plans for the hot FP32 line lengths.
-    if constexpr (sizeof(T) == 4) if (a.pl.E == 16) {
+    if constexpr (sizeof(T) == 4) if (a.pl.E == 16 && !a.force_runtime) {
         switch (a.pl.L) {
         case 256: return run(k_ypass<T, 16, INV, 256>, a, grid, block, smem, s);
         case 512: return run(k_ypass<T, 16, INV, 512>, a, grid, block, smem, s);

@@ -17,7 +17,7 @@ static cudaError_t run(K kernel, const ZArgs<T> &a, unsigned grid, unsigned bloc
 
 // Compile-time plans for the hot FP32 row lengths, the run-time plan otherwise.
 #define PSOLVE_Z_DISPATCH(KERNEL)                                                   \
-    if constexpr (sizeof(T) == 4) if (a.pl.E == 16) {                               \
+    if constexpr (sizeof(T) == 4) if (a.pl.E == 16 && !a.force_runtime) {                               \
         switch (a.pl.L) {                                                           \
         case 256: return run<T, 16>(KERNEL<T, 16, 256>, a, grid, block, smem, s);   \
         case 512: return run<T, 16>(KERNEL<T, 16, 512>, a, grid, block, smem, s);   \

@@ -136,6 +136,13 @@ class Plan:
         _lib.check(rc, "psolve_debug_kvec")
         return out
 
+    def autotune(self, stream=None) -> None:
+        """Time tile/plan candidates on scratch data and keep the fastest
+        (persisted in the per-GPU tuning cache)."""
+        with torch.cuda.device(self.device):
+            rc = self.lib.psolve_autotune(self.handle, _stream_handle(stream, self.device))
+        _lib.check(rc, "psolve_autotune")
+
     def set_profiling(self, enable: bool) -> None:
         _lib.check(self.lib.psolve_set_profiling(self.handle, int(bool(enable))), "psolve_set_profiling")
 
