@@ -42,6 +42,10 @@ def parse():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--grid", type=int, default=512)
+    ap.add_argument("--workload", choices=["sharp", "batch64"], default="sharp",
+                    help="sharp: one FP32 grid^3 solve per step (default, 512^3); batch64: the 64 "
+                         "uneven radix-2/3 grids in one persistent launch per step")
+    ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
 
@@ -127,9 +131,10 @@ def kernel_digest() -> str:
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(kernel: str, grid: int):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it
-    was taken on the current kernel sources; else None."""
+def recorded_traffic(pass_name: str, unknowns: int):
+    """DRAM bytes per launch of the pass's kernel from the committed ncu
+    summary (profiles/ncu_traffic.json), scaled to `unknowns` if the capture
+    was smaller, and only if it was taken on the current kernel sources."""
     p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     if not os.path.exists(p):
         return None
@@ -137,11 +142,10 @@ def recorded_traffic(kernel: str, grid: int):
         d = json.load(fh)
     if d.get("kernel_digest") != kernel_digest():
         return None
-    e = d.get("kernels", {}).get(kernel)
+    e = d.get("passes", {}).get(pass_name)
     if not e:
         return None
-    scale = (grid ** 3) / float(e.get("unknowns", grid ** 3))
-    return float(e["dram_bytes_per_launch"]) * scale
+    return float(e["dram_bytes_per_launch"]) * unknowns / float(e["unknowns"])
 
 
 # --------------------------------------------------------------- oracle
@@ -234,6 +238,8 @@ def run_ours(args):
     f = f_pin.to(dev)
     u = torch.empty_like(f)
     plan = Plan(shape, dtype="f32", device=dev)
+    if not args.no_autotune:
+        plan.autotune()
     stream = torch.cuda.current_stream(dev)
 
     def barrier():
@@ -291,9 +297,7 @@ def run_ours(args):
     peak, peak_kind = peaks()
     algo_bytes = BYTES_PER_UNKNOWN_PER_PASS * N
     achieved = algo_bytes / (avg[top] * 1e-3) / 1e9
-    kernel_name = {"zfwd": "k_zfwd", "yfwd": "k_ypass", "xdiv": "k_xfused", "yinv": "k_ypass",
-                   "zinv": "k_zinv"}[top]
-    traffic = recorded_traffic(kernel_name, n)
+    traffic = recorded_traffic(top, N)
 
     if rank != 0:
         return 0
@@ -328,10 +332,93 @@ def run_ours(args):
     return 0
 
 
+# ------------------------------------------------------------ batch of 64
+def run_batch(args):
+    """64 uneven grids (axes from {24..256}) per step in one persistent launch,
+    next to the same 64 solves issued one plan per instance (the plain FP32
+    single-solve path)."""
+    import torch
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_1408_6497_gb300 import Plan, build
+    from paper_1408_6497_gb300 import workloads as wl
+    build.build()
+    shapes = wl.batch_shapes(64)
+    N = sum(int(np.prod(s)) for s in shapes)
+    plan = Plan(dtype="f32", shapes=shapes, device=dev)
+    if not args.no_autotune:
+        plan.autotune()
+    flat = plan.empty()
+    for b, s in enumerate(shapes):
+        plan.view(flat, b).copy_(torch.from_numpy(wl.batch_instance(s, b).f.astype(np.float32)))
+    u = torch.empty_like(flat)
+    singles = [Plan(s, dtype="f32", device=dev) for s in shapes]
+    if not args.no_autotune:
+        for sp in singles:
+            sp.autotune()
+    views_f = [plan.view(flat, b).reshape(-1) for b in range(64)]
+    views_u = [plan.view(u, b).reshape(-1) for b in range(64)]
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(max(3, args.warmup)):
+        plan.execute(flat, u)
+        for b, sp in enumerate(singles):
+            sp.execute(views_f[b], views_u[b])
+    torch.cuda.synchronize(dev)
+    sampler = ClockSampler(gpu_uuid(torch, dev))
+    sampler.start()
+    e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    e0.record(stream)
+    for _ in range(args.steps):
+        plan.execute(flat, u)
+    e1.record(stream)
+    for _ in range(args.steps):
+        for b, sp in enumerate(singles):
+            sp.execute(views_f[b], views_u[b])
+    e2.record(stream)
+    torch.cuda.synchronize(dev)
+    clocks = sampler.stop()
+    t_batch = e0.elapsed_time(e1) / args.steps
+    t_single = e1.elapsed_time(e2) / args.steps
+    peak, peak_kind = peaks()
+    algo = 5 * BYTES_PER_UNKNOWN_PER_PASS * N
+    achieved = algo / (t_batch * 1e-3) / 1e9
+    h_pin = flat.cpu().pin_memory()
+    o_pin = torch.empty_like(h_pin).pin_memory()
+    plan.execute_host(h_pin, o_pin)
+    h0 = time.perf_counter()
+    for _ in range(5):
+        plan.execute_host(h_pin, o_pin)
+    e2e_s = (time.perf_counter() - h0) / 5
+    line = {
+        "impl": "ours", "metric": METRIC, "value": N / (t_batch * 1e-3), "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_batch, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "batch64: 64 FP32 grids, axes drawn from {24,32,48,64,96,128,192,256}, "
+                               "16 periodised Gaussians each, one persistent launch per step",
+                   "unknowns": N, "l2": "working set 255 MiB > L2, no flush"},
+        "roofline": {"bound": "hbm", "kernel": "batched", "achieved": achieved, "peak": peak,
+                     "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                     "algorithmic_bytes_per_launch": algo},
+        "single_solve_loop": {"value": N / (t_single * 1e-3), "ms_per_step": t_single,
+                              "launches_per_step": sum(sp.launches_per_solve for sp in singles)},
+        "batched_vs_single_solve_loop": t_single / t_batch,
+        "e2e": {"value": N / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 4 * plan.total,
+                "d2h_bytes_per_step": 4 * plan.total},
+        "gpu_launches": plan.launches_per_solve * args.steps,
+        "clocks": clocks,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batch64":
+        return run_batch(args)
     return run_ours(args)
 
 

@@ -50,8 +50,6 @@ struct Group {
     size_t tw_z, tw_y, tw_x, post; // complex-element offsets into the table buffer
     int Wz, Wy, Wx;
     int cfg_y, cfg_x;    // TMA configuration of the y / x pass (-1: per-tile kernel)
-    int bWz, bWy, bWx;   // tile widths inside the persistent batched launch (0: default)
-    int order;           // radix order of the run-time stage plans (see make_line_plan)
 };
 
 bool factor23(int n, int &a, int &b)
@@ -73,11 +71,11 @@ bool size_ok(int n)
 // the largest power-of-two radices (<= 16) that divide E (order 0).  Order 1
 // runs the same radices in reverse, order 2 puts the radix-3 stages last;
 // any order is a valid Stockham factorisation, and the autotuner times them.
-bool make_line_plan(int L, LinePlan &p, int order = 0)
+bool make_line_plan(int L, LinePlan &p, int order = 0, int e3cap = 3)
 {
     int a, b;
     if (!factor23(L, a, b) || L < 2) return false;
-    const int E = b > 0 ? 3 * (1 << std::min(a, 3)) : (1 << std::min(a, 4));
+    const int E = b > 0 ? 3 * (1 << std::min(a, e3cap)) : (1 << std::min(a, 4));
     if (!supported_E(E)) return false;
     std::memset(&p, 0, sizeof(p));
     p.L = L;
@@ -230,6 +228,7 @@ struct psolve_plan {
     void *g_u;
     unsigned long long wait_ns;
     unsigned long long g_wait;
+    int bknob[6]; // batched launch: tile-width divisor (z, y, x) and radix order (z, y, x)
     // per-pass profiling: one set of kPasses+1 events per recorded solve
     bool profiling;
     std::vector<std::vector<cudaEvent_t>> ev_used;
@@ -375,53 +374,62 @@ void write_tune_cache(const std::map<std::string, TuneChoice> &m)
     std::rename(tmp.c_str(), path.c_str());
 }
 
+// Key of a batched plan: FNV-1a over its instance shapes.
+std::string batch_key(const psolve_plan *p)
+{
+    unsigned long long h = 1469598103934665603ull;
+    for (const auto &g : p->groups)
+        for (int v : {g.nx, g.ny, g.nz}) {
+            h ^= (unsigned long long)v;
+            h *= 1099511628211ull;
+        }
+    char buf[32];
+    std::snprintf(buf, sizeof(buf), "%016llx", h);
+    return gpu_key(p->device) + "|" + std::to_string(p->dtype) + "|batch|" + buf;
+}
+
 // Apply cached choices that are still valid for this plan.
 void apply_tuning_cache(psolve_plan *p)
 {
     const auto m = read_tune_cache();
     if (m.empty()) return;
+    if (!p->uniform) {
+        // knobs are stored as three entries: divisors, orders (W, cfg, order per axis)
+        for (int axis = 0; axis < 3; ++axis) {
+            auto it = m.find(batch_key(p) + "|" + "zyx"[axis]);
+            if (it == m.end()) continue;
+            if (it->second.W >= 1 && it->second.W <= 8) p->bknob[axis] = it->second.W;
+            if (it->second.order >= 0 && it->second.order <= 2) p->bknob[3 + axis] = it->second.order;
+        }
+        return;
+    }
     const bool fp64 = p->dtype == PSOLVE_F64;
-    const bool uniform = p->uniform;
     for (auto &g : p->groups) {
-        const char *path = uniform ? "pass" : "batch";
+        const char *path = "pass";
         auto it = m.find(tune_key(p, path, 'z', g.M, g.M));
         if (it != m.end() && it->second.W >= 1) {
             const int keep = g.Wz;
-            if (uniform) g.Wz = it->second.W; else g.bWz = it->second.W;
-            if (uniform && (g.Wz * g.pz.TL > max_threads(fp64, g.pz.E) || z_smem(g, p->dtype) > kSmemCap)) g.Wz = keep;
-            LinePlan pl;
-            if (!uniform && make_line_plan(g.M, pl, it->second.order)) g.pz = pl;
+            g.Wz = it->second.W;
+            if (g.Wz * g.pz.TL > max_threads(fp64, g.pz.E) || z_smem(g, p->dtype) > kSmemCap) g.Wz = keep;
         }
         it = m.find(tune_key(p, path, 'y', g.ny, g.M));
         if (it != m.end()) {
             const TuneChoice c = it->second;
-            if (uniform) {
-                if (c.cfg >= 0 && tma_fits(p, g.ny, g.M, c.cfg)) g.cfg_y = c.cfg;
-                else if (c.cfg < 0 && c.W >= 1 && c.W <= g.M && c.W * g.py.TL <= max_threads(fp64, g.py.E) &&
-                         s_smem(g.ny, c.W, p->dtype) <= kSmemCap) {
-                    g.cfg_y = -1;
-                    g.Wy = c.W;
-                }
-            } else {
-                g.bWy = c.W;
-                LinePlan pl;
-                if (make_line_plan(g.ny, pl, c.order)) g.py = pl;
+            if (c.cfg >= 0 && tma_fits(p, g.ny, g.M, c.cfg)) g.cfg_y = c.cfg;
+            else if (c.cfg < 0 && c.W >= 1 && c.W <= g.M && c.W * g.py.TL <= max_threads(fp64, g.py.E) &&
+                     s_smem(g.ny, c.W, p->dtype) <= kSmemCap) {
+                g.cfg_y = -1;
+                g.Wy = c.W;
             }
         }
         it = m.find(tune_key(p, path, 'x', g.nx, g.M));
         if (it != m.end()) {
             const TuneChoice c = it->second;
-            if (uniform) {
-                if (c.cfg >= 0 && tma_fits(p, g.nx, g.M, c.cfg)) g.cfg_x = c.cfg;
-                else if (c.cfg < 0 && c.W >= 2 && c.W * g.px.TL <= max_threads(fp64, g.px.E) &&
-                         s_smem(g.nx, c.W, p->dtype) <= kSmemCap) {
-                    g.cfg_x = -1;
-                    g.Wx = c.W;
-                }
-            } else {
-                g.bWx = c.W;
-                LinePlan pl;
-                if (make_line_plan(g.nx, pl, c.order)) g.px = pl;
+            if (c.cfg >= 0 && tma_fits(p, g.nx, g.M, c.cfg)) g.cfg_x = c.cfg;
+            else if (c.cfg < 0 && c.W >= 2 && c.W * g.px.TL <= max_threads(fp64, g.px.E) &&
+                     s_smem(g.nx, c.W, p->dtype) <= kSmemCap) {
+                g.cfg_x = -1;
+                g.Wx = c.W;
             }
         }
     }
@@ -439,6 +447,12 @@ template <typename T> psolve_status setup_batched(psolve_plan *p)
     std::vector<BatchSeg<T>> segs(5 * (size_t)B);
     long long first = 0;
     size_t smem = 0;
+    // Line plans in the radix order the knobs select (the tables are per length).
+    for (auto &g : p->groups) {
+        make_line_plan(g.M, g.pz, p->bknob[3], 2);
+        make_line_plan(g.ny, g.py, p->bknob[4], 2);
+        make_line_plan(g.nx, g.px, p->bknob[5], 2);
+    }
     for (int pass = 0; pass < 5; ++pass) {
         for (int i = 0; i < B; ++i) {
             const Group &g = p->groups[i];
@@ -449,7 +463,7 @@ template <typename T> psolve_status setup_batched(psolve_plan *p)
             sg.off = (long long)g.off0;
             const int M = g.M;
             if (pass == 0 || pass == 4) {
-                int W = g.bWz > 0 ? std::min(g.bWz, std::max(1, NT / g.pz.TL)) : std::max(1, NT / g.pz.TL);
+                int W = std::max(1, NT / g.pz.TL / p->bknob[0]);
                 const int LP = M + (M >> 4) + 1;
                 while (W > 1 && (size_t)(M + (size_t)W * LP) * cs > kSmemCap) W /= 2;
                 sg.E = g.pz.E;
@@ -463,8 +477,7 @@ template <typename T> psolve_status setup_batched(psolve_plan *p)
                 sg.ntiles = (sg.z.rows + W - 1) / W;
                 smem = std::max(smem, (size_t)(M + (size_t)W * LP) * cs);
             } else if (pass == 1 || pass == 3) {
-                int W = std::min(M, std::max(1, NT / g.py.TL));
-                if (g.bWy > 0) W = std::min(W, g.bWy);
+                int W = std::min(M, std::max(1, NT / g.py.TL / p->bknob[1]));
                 while (W > 1 && s_smem(g.ny, W, p->dtype) > kSmemCap) W /= 2;
                 sg.E = g.py.E;
                 sg.y.nplanes = g.nx;
@@ -478,8 +491,7 @@ template <typename T> psolve_status setup_batched(psolve_plan *p)
                 sg.ntiles = (long long)g.nx * sg.y.ncb;
                 smem = std::max(smem, s_smem(g.ny, W, p->dtype));
             } else {
-                int W = std::max(2, std::min(std::max(2, M), NT / g.px.TL));
-                if (g.bWx > 0) W = std::max(2, std::min(W, g.bWx));
+                int W = std::max(2, std::min(std::max(2, M), NT / g.px.TL / p->bknob[2]));
                 while (W > 2 && s_smem(g.nx, W, p->dtype) > kSmemCap) W /= 2;
                 if (W * g.px.TL > NT) return fail(PSOLVE_ERR_UNSUPPORTED_SIZE, "x line too long for a batch tile");
                 sg.E = g.px.E;
@@ -560,6 +572,7 @@ psolve_status build_plan(const std::vector<int> &nx, const std::vector<int> &ny,
     p->grid_batched = 0;
     p->wait_ns = 2000000000ull;
     p->g_wait = 0;
+    for (int k = 0; k < 6; ++k) p->bknob[k] = k < 3 ? 1 : 0;
     size_t off = 0;
     for (int b = 0; b < batch; ++b) {
         const size_t N = (size_t)nx[b] * ny[b] * nz[b];
@@ -588,7 +601,11 @@ psolve_status build_plan(const std::vector<int> &nx, const std::vector<int> &ny,
     std::map<int, size_t> post_at;  // nz -> offset
     size_t tcount = 0;
     for (auto &g : p->groups) {
-        if (!make_line_plan(g.M, g.pz) || !make_line_plan(g.ny, g.py) || !make_line_plan(g.nx, g.px))
+        // Unequal grids share the persistent batched kernel, which holds at
+        // most 16 points per thread (12 for lengths 3·2^a).
+        const int e3cap = uniform ? 3 : 2;
+        if (!make_line_plan(g.M, g.pz, 0, e3cap) || !make_line_plan(g.ny, g.py, 0, e3cap) ||
+            !make_line_plan(g.nx, g.px, 0, e3cap))
             return fail(PSOLVE_ERR_UNSUPPORTED_SIZE, "no stage plan for this size");
         choose_tiles(g, dtype);
         for (int L : {g.M, g.ny, g.nx})
@@ -919,6 +936,77 @@ psolve_status solve(psolve_plan *p, const void *f, void *u, void *stream)
 
 
 // ------------------------------------------------------------- autotuner
+psolve_status run_batched(psolve_plan *p, const void *f, void *u, cudaStream_t s);
+
+void drop_batched(psolve_plan *p)
+{
+    if (p->gexec) cudaGraphExecDestroy(p->gexec);
+    if (p->graph) cudaGraphDestroy(p->graph);
+    if (p->segs_dev) cudaFree(p->segs_dev);
+    if (p->counters) cudaFree(p->counters);
+    p->gexec = nullptr;
+    p->graph = nullptr;
+    p->segs_dev = nullptr;
+    p->counters = nullptr;
+    p->batched = false;
+}
+
+// The persistent batched launch is tuned as a whole: coordinate descent over
+// its plan-wide knobs (tile-width divisor and radix order per axis), each
+// candidate timed as complete batched solves on scratch buffers.
+psolve_status autotune_batched(psolve_plan *p, cudaStream_t s, std::map<std::string, TuneChoice> &cache)
+{
+    const size_t bytes = p->total * rsize(p->dtype);
+    void *f = nullptr, *u = nullptr;
+    if (cudaMalloc(&f, bytes) != cudaSuccess) return fail(PSOLVE_ERR_OOM, "autotune scratch");
+    if (cudaMalloc(&u, bytes) != cudaSuccess) {
+        cudaFree(f);
+        return fail(PSOLVE_ERR_OOM, "autotune scratch");
+    }
+    cudaMemsetAsync(f, 0x3c, bytes, s);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const bool prof = p->profiling;
+    p->profiling = false;
+    auto measure = [&]() -> float {
+        drop_batched(p);
+        if (setup_batched<float>(p) != PSOLVE_OK) return 1e30f;
+        if (run_batched(p, f, u, s) != PSOLVE_OK) return 1e30f;
+        cudaEventRecord(e0, s);
+        for (int r = 0; r < 3; ++r) run_batched(p, f, u, s);
+        cudaEventRecord(e1, s);
+        if (cudaEventSynchronize(e1) != cudaSuccess) return 1e30f;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        return ms / 3;
+    };
+    float best = measure();
+    const int choices[6][3] = {{1, 2, 4}, {1, 2, 4}, {1, 2, 4}, {0, 1, 2}, {0, 1, 2}, {0, 1, 2}};
+    for (int round = 0; round < 2; ++round)
+        for (int k = 0; k < 6; ++k) {
+            const int keep = p->bknob[k];
+            int bv = keep;
+            for (int c : choices[k]) {
+                if (c == keep) continue;
+                p->bknob[k] = c;
+                const float t = measure();
+                if (t < best) { best = t; bv = c; }
+            }
+            p->bknob[k] = bv;
+        }
+    drop_batched(p);
+    psolve_status st = setup_batched<float>(p);
+    p->profiling = prof;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaStreamSynchronize(s);
+    cudaFree(f);
+    cudaFree(u);
+    for (int axis = 0; axis < 3; ++axis)
+        cache[batch_key(p) + "|" + "zyx"[axis]] = TuneChoice{p->bknob[axis], -1, p->bknob[3 + axis]};
+    return st;
+}
 // Times candidate tile widths, TMA configurations and radix orders of each
 // pass on a scratch instance and keeps the fastest (the analogue of the FFT
 // library "MEASURE" planning the paper's setup phase pays once, §3 Table 1).
@@ -952,7 +1040,7 @@ template <typename T> psolve_status autotune_impl(psolve_plan *p, cudaStream_t s
         Group gt = g;
         gt.count = 1;
         gt.off0 = 0;
-        if (!p->batched) {
+        if (!p->batched && p->uniform) {
             // z rows per block
             float best = inf;
             int bw = g.Wz;
@@ -990,66 +1078,13 @@ template <typename T> psolve_status autotune_impl(psolve_plan *p, cudaStream_t s
                 else { g.cfg_x = gt.cfg_x = bcfg; g.Wx = gt.Wx = bW; }
                 cache[tune_key(p, "pass", axis == 0 ? 'y' : 'x', L, g.M)] = TuneChoice{bW, bcfg, 0};
             }
-        } else {
-            // Inside the persistent launch: tile widths that fit its blocks and
-            // the radix order of each line's run-time plan.
-            gt.cfg_y = gt.cfg_x = -1;
-            for (int axis = 0; axis < 3; ++axis) {
-                const int L = axis == 0 ? g.M : (axis == 1 ? g.ny : g.nx);
-                const char key = axis == 0 ? 'z' : (axis == 1 ? 'y' : 'x');
-                float bt = inf;
-                int bW = 0, bo = 0;
-                for (int order = 0; order < 3; ++order) {
-                    LinePlan pl;
-                    if (!make_line_plan(L, pl, order)) continue;
-                    const int wmax = std::max(axis == 2 ? 2 : 1, kBatchThreads / pl.TL);
-                    for (int d = 1; d <= 4; d *= 2) {
-                        int W = std::max(axis == 2 ? 2 : 1, wmax / d);
-                        if (axis != 0) W = std::min(W, std::max(axis == 2 ? 2 : 1, g.M));
-                        float t;
-                        if (axis == 0) {
-                            gt.pz = pl;
-                            gt.Wz = W;
-                            if (z_smem(gt, p->dtype) > kSmemCap) continue;
-                            t = timed(gt, 0, true) + timed(gt, 4, true);
-                        } else if (axis == 1) {
-                            gt.py = pl;
-                            gt.Wy = W;
-                            if (s_smem(L, W, p->dtype) > kSmemCap) continue;
-                            t = timed(gt, 1, true);
-                        } else {
-                            gt.px = pl;
-                            gt.Wx = W;
-                            if (s_smem(L, W, p->dtype) > kSmemCap) continue;
-                            t = timed(gt, 2, true);
-                        }
-                        if (t < bt) { bt = t; bW = W; bo = order; }
-                    }
-                }
-                LinePlan best;
-                make_line_plan(L, best, bo);
-                if (axis == 0) { g.pz = gt.pz = best; g.bWz = bW; gt.Wz = bW; }
-                else if (axis == 1) { g.py = gt.py = best; g.bWy = bW; gt.Wy = bW; }
-                else { g.px = gt.px = best; g.bWx = bW; gt.Wx = bW; }
-                cache[tune_key(p, "batch", key, L, g.M)] = TuneChoice{bW, -1, bo};
-            }
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaFree(buf);
     if (p->batched) {
-        // Rebuild the segment table and its graph with the new choices.
-        if (p->gexec) cudaGraphExecDestroy(p->gexec);
-        if (p->graph) cudaGraphDestroy(p->graph);
-        if (p->segs_dev) cudaFree(p->segs_dev);
-        if (p->counters) cudaFree(p->counters);
-        p->gexec = nullptr;
-        p->graph = nullptr;
-        p->segs_dev = nullptr;
-        p->counters = nullptr;
-        p->batched = false;
-        psolve_status st = setup_batched<float>(p);
+        psolve_status st = autotune_batched(p, s, cache);
         if (st != PSOLVE_OK) return st;
     }
     write_tune_cache(cache);

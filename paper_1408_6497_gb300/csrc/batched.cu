@@ -10,11 +10,16 @@
 // something is broken, and it is bounded in time all the same (the block
 // then records PSOLVE_ERR_TIMEOUT in the status word and leaves).
 // Data written by other blocks of the same launch are read with L2-only
-// loads (ld.global.cg).  Lines whose points-per-thread is not one of
-// 4, 8, 12, 16, 24 are not covered (the planner then launches per pass).
+// loads (ld.global.cg).  Lines are planned with at most 16 points per
+// thread (12 for lengths 3·2^a); lines needing 2, 3 or 6 are not covered
+// (the planner then launches per pass).
 #include "psolve.h"
 #include "launch.h"
 #include "tma.cuh"
+
+#ifndef PSOLVE_BATCH_MINB
+#define PSOLVE_BATCH_MINB 2
+#endif
 
 namespace psolve {
 
@@ -42,65 +47,46 @@ __device__ bool wait_count(const int *counter, long long need, unsigned long lon
 template <typename T, int E> __device__ __forceinline__ void run_item(const BatchSeg<T> &sg, long long tile,
                                                                     const T *f, T *u, unsigned char *smem)
 {
+    T *ui = u + sg.off;
     switch (sg.kind) {
-    case 0: {
-        ZArgs<T> a = sg.z;
-        a.in = f + sg.off;
-        a.out = u + sg.off;
-        zfwd_tile<T, E, 0, true>(a, tile, smem);
-        break;
-    }
-    case 1:
-    case 3: {
-        SArgs<T> a = sg.y;
-        a.data = u + sg.off;
-        if (sg.kind == 1) ypass_tile<T, E, false, 0, true>(a, tile, smem);
-        else ypass_tile<T, E, true, 0, true>(a, tile, smem);
-        break;
-    }
-    case 2: {
-        XArgs<T> a = sg.x;
-        a.data = u + sg.off;
-        xfused_tile<T, E, 0, true>(a, tile, smem);
-        break;
-    }
-    default: {
-        ZArgs<T> a = sg.z;
-        a.in = u + sg.off;
-        a.out = u + sg.off;
-        zinv_tile<T, E, 0, true>(a, tile, smem);
-        break;
-    }
+    case 0: zfwd_tile<T, E, 0, true>(sg.z, f + sg.off, ui, tile, smem); break;
+    case 1: ypass_tile<T, E, false, 0, true>(sg.y, ui, tile, smem); break;
+    case 2: xfused_tile<T, E, 0, true>(sg.x, ui, tile, smem); break;
+    case 3: ypass_tile<T, E, true, 0, true>(sg.y, ui, tile, smem); break;
+    default: zinv_tile<T, E, 0, true>(sg.z, ui, ui, tile, smem); break;
     }
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kBatchThreads) k_batched(const BatchSeg<T> *__restrict__ segs, int nseg,
-                                                           long long total, const T *f, T *u,
-                                                           unsigned long long *work, int *done, int *status,
-                                                           unsigned long long wait_ns)
+__global__ void __launch_bounds__(kBatchThreads, PSOLVE_BATCH_MINB) k_batched(const BatchSeg<T> *__restrict__ segs, int nseg,
+                                                              long long total, const T *f, T *u,
+                                                              unsigned long long *work, int *done, int *status,
+                                                              unsigned long long wait_ns)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
-    __shared__ long long s_item;
+    __shared__ long long s_item, s_next;
     __shared__ int s_seg, s_abort;
+    if (threadIdx.x == 0) {
+        s_next = (long long)atomicAdd(work, 1ull);
+        s_seg = 0;
+    }
     while (true) {
         __syncthreads(); // the previous item's shared-memory reads are finished
         if (threadIdx.x == 0) {
-            s_item = (long long)atomicAdd(work, 1ull);
+            s_item = s_next;
             s_abort = 0;
             if (s_item < total) {
-                int lo = 0, hi = nseg - 1;
-                while (lo < hi) {
-                    const int mid = (lo + hi + 1) >> 1;
-                    if (segs[mid].first <= s_item) lo = mid;
-                    else hi = mid - 1;
-                }
-                s_seg = lo;
-                const int dep = segs[lo].dep;
-                if (dep >= 0 && !wait_count(&done[dep], segs[lo].need, wait_ns)) {
+                // Items grow per block: walk forward from the last segment.
+                int sgi = s_seg;
+                while (sgi + 1 < nseg && segs[sgi + 1].first <= s_item) ++sgi;
+                s_seg = sgi;
+                const int dep = segs[sgi].dep;
+                if (dep >= 0 && !wait_count(&done[dep], segs[sgi].need, wait_ns)) {
                     s_abort = 1;
                     atomicExch(status, (int)PSOLVE_ERR_TIMEOUT);
                 }
+                // Take the next item now; it is only claimed, not started.
+                s_next = (long long)atomicAdd(work, 1ull);
             }
         }
         __syncthreads();
@@ -113,7 +99,6 @@ __global__ void __launch_bounds__(kBatchThreads) k_batched(const BatchSeg<T> *__
         case 8: run_item<T, 8>(sg, tile, f, u, smraw); break;
         case 12: run_item<T, 12>(sg, tile, f, u, smraw); break;
         case 16: run_item<T, 16>(sg, tile, f, u, smraw); break;
-        case 24: run_item<T, 24>(sg, tile, f, u, smraw); break;
         default: break;
         }
         // Publish this tile: every thread's stores, then one release count.
@@ -135,6 +120,6 @@ template <typename T> cudaError_t batched_prepare(size_t smem)
 }
 template cudaError_t batched_prepare<float>(size_t);
 
-bool batched_supports_E(int E) { return E == 4 || E == 8 || E == 12 || E == 16 || E == 24; }
+bool batched_supports_E(int E) { return E == 4 || E == 8 || E == 12 || E == 16; }
 
 } // namespace psolve

@@ -87,7 +87,8 @@ template <bool CG, typename C> __device__ __forceinline__ C ld_data(const C *p)
 
 // --------------------------------------------------------------- z forward
 template <typename T, int E, int LC, bool CG = false>
-__device__ __forceinline__ void zfwd_tile(const ZArgs<T> &a, long long tile, unsigned char *smem)
+__device__ __forceinline__ void zfwd_tile(const ZArgs<T> &a, const T *in, T *out, long long tile,
+                                          unsigned char *smem)
 {
     using C = typename cplx_of<T>::type;
     C *stw = reinterpret_cast<C *>(smem);
@@ -101,7 +102,7 @@ __device__ __forceinline__ void zfwd_tile(const ZArgs<T> &a, long long tile, uns
     for (int i = tid; i < M; i += blockDim.x) stw[i] = a.tw[i];
     C v[E];
     if (active) {
-        const C *src = reinterpret_cast<const C *>(a.in + row * (2 * M)) + t;
+        const C *src = reinterpret_cast<const C *>(in + row * (2 * M)) + t;
 #pragma unroll
         for (int m = 0; m < E; ++m) v[m] = ld_data<CG>(src + m * TL);
     } else {
@@ -119,7 +120,7 @@ __device__ __forceinline__ void zfwd_tile(const ZArgs<T> &a, long long tile, uns
     }
     __syncthreads();
     if (active) {
-        C *dst = reinterpret_cast<C *>(a.out) + row * M;
+        C *dst = reinterpret_cast<C *>(out) + row * M;
         const T half = (T)0.5;
 #pragma unroll
         for (int m = 0; m < E; ++m) {
@@ -139,7 +140,8 @@ __device__ __forceinline__ void zfwd_tile(const ZArgs<T> &a, long long tile, uns
 
 // --------------------------------------------------------------- z inverse
 template <typename T, int E, int LC, bool CG = false>
-__device__ __forceinline__ void zinv_tile(const ZArgs<T> &a, long long tile, unsigned char *smem)
+__device__ __forceinline__ void zinv_tile(const ZArgs<T> &a, const T *in, T *out, long long tile,
+                                          unsigned char *smem)
 {
     using C = typename cplx_of<T>::type;
     C *stw = reinterpret_cast<C *>(smem);
@@ -155,7 +157,7 @@ __device__ __forceinline__ void zinv_tile(const ZArgs<T> &a, long long tile, uns
     const int LP = M + (M >> 4) + 1;
     const MapRow map{w * LP};
     if (active) {
-        const C *src = reinterpret_cast<const C *>(a.in) + row * M + t;
+        const C *src = reinterpret_cast<const C *>(in) + row * M + t;
 #pragma unroll
         for (int m = 0; m < E; ++m) v[m] = ld_data<CG>(src + m * TL);
 #pragma unroll
@@ -183,7 +185,7 @@ __device__ __forceinline__ void zinv_tile(const ZArgs<T> &a, long long tile, uns
     __syncthreads(); // partner reads done before the transform reuses the buffer
     line_fft_any<true, LC>(v, t, a.pl, stw, sx, map, active);
     if (active) {
-        C *dst = reinterpret_cast<C *>(a.out + row * (2 * M)) + t;
+        C *dst = reinterpret_cast<C *>(out + row * (2 * M)) + t;
 #pragma unroll
         for (int m = 0; m < E; ++m) dst[m * TL] = v[m];
     }
@@ -191,7 +193,7 @@ __device__ __forceinline__ void zinv_tile(const ZArgs<T> &a, long long tile, uns
 
 // ------------------------------------------------------- strided c2c (y)
 template <typename T, int E, bool INV, int LC, bool CG = false>
-__device__ __forceinline__ void ypass_tile(const SArgs<T> &a, long long tile, unsigned char *smem)
+__device__ __forceinline__ void ypass_tile(const SArgs<T> &a, T *data, long long tile, unsigned char *smem)
 {
     using C = typename cplx_of<T>::type;
     C *stw = reinterpret_cast<C *>(smem);
@@ -205,7 +207,7 @@ __device__ __forceinline__ void ypass_tile(const SArgs<T> &a, long long tile, un
     const int col = cb * W + w;
     const bool active = (col < a.M) && (t < TL);
     for (int i = tid; i < L; i += blockDim.x) stw[i] = a.tw[i];
-    C *base = reinterpret_cast<C *>(a.data) + plane * a.sPlane + col + (long long)t * a.sL;
+    C *base = reinterpret_cast<C *>(data) + plane * a.sPlane + col + (long long)t * a.sL;
     const long long step = (long long)TL * a.sL;
     C v[E];
     if (active) {
@@ -297,7 +299,7 @@ __device__ __forceinline__ void xpair_block(T *data, int nx_rt, int ny, int M, l
 // Tiles [0, main_tiles) are (instance, y, column block); the following ones
 // are groups of packed-column pairs.
 template <typename T, int E, int LC, bool CG = false>
-__device__ __forceinline__ void xfused_tile(const XArgs<T> &a, long long tile, unsigned char *smem)
+__device__ __forceinline__ void xfused_tile(const XArgs<T> &a, T *data, long long tile, unsigned char *smem)
 {
     using C = typename cplx_of<T>::type;
     C *stw = reinterpret_cast<C *>(smem);
@@ -312,7 +314,7 @@ __device__ __forceinline__ void xfused_tile(const XArgs<T> &a, long long tile, u
     const MapStrided map{W, w};
 
     if (tile >= a.main_tiles) {
-        xpair_block<T, E, LC, CG>(a.data, nx, ny, M, a.sInst, a.npairs, a.coef, a.pl, W, TL, tile - a.main_tiles,
+        xpair_block<T, E, LC, CG>(data, nx, ny, M, a.sInst, a.npairs, a.coef, a.pl, W, TL, tile - a.main_tiles,
                                   t, w, stw, sx);
         return;
     }
@@ -323,7 +325,7 @@ __device__ __forceinline__ void xfused_tile(const XArgs<T> &a, long long tile, u
     const long long b = rest / ny;
     const int col = cb * W + w;
     const bool active = (col < M) && (t < TL);
-    C *base = reinterpret_cast<C *>(a.data) + b * a.sInst + (long long)y * M + col + (long long)t * sL;
+    C *base = reinterpret_cast<C *>(data) + b * a.sInst + (long long)y * M + col + (long long)t * sL;
     if (active) {
 #pragma unroll
         for (int m = 0; m < E; ++m) v[m] = ld_data<CG>(base + m * step);
@@ -354,28 +356,28 @@ template <typename T, int E, int LC>
 __global__ void __launch_bounds__(Bound<T, E, LC>::value, Bound<T, E, LC>::minb) k_zfwd(ZArgs<T> a)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
-    zfwd_tile<T, E, LC>(a, blockIdx.x, smraw);
+    zfwd_tile<T, E, LC>(a, a.in, a.out, blockIdx.x, smraw);
 }
 
 template <typename T, int E, int LC>
 __global__ void __launch_bounds__(Bound<T, E, LC>::value, Bound<T, E, LC>::minb) k_zinv(ZArgs<T> a)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
-    zinv_tile<T, E, LC>(a, blockIdx.x, smraw);
+    zinv_tile<T, E, LC>(a, a.in, a.out, blockIdx.x, smraw);
 }
 
 template <typename T, int E, bool INV, int LC>
 __global__ void __launch_bounds__(Bound<T, E, LC>::value, Bound<T, E, LC>::minb) k_ypass(SArgs<T> a)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
-    ypass_tile<T, E, INV, LC>(a, blockIdx.x, smraw);
+    ypass_tile<T, E, INV, LC>(a, a.data, blockIdx.x, smraw);
 }
 
 template <typename T, int E, int LC>
 __global__ void __launch_bounds__(Bound<T, E, LC>::value, Bound<T, E, LC>::minb) k_xfused(XArgs<T> a)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
-    xfused_tile<T, E, LC>(a, blockIdx.x, smraw);
+    xfused_tile<T, E, LC>(a, a.data, blockIdx.x, smraw);
 }
 
 } // namespace psolve
