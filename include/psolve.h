@@ -179,6 +179,14 @@ psolve_status psolve_debug_set_wait(psolve_plan *plan, unsigned long long wait_n
 psolve_status psolve_execute_noalloc(int nx, int ny, int nz, int dtype, const void *f, void *u,
                                      void *stream);
 
+/* Test hook for the tensor-core radix-16 stage used by PSOLVE_F32_TC: for
+ * each of `nbutterflies` rows of 16 complex FP32 values (in, device,
+ * interleaved re/im, row-major), out = F·in with F[k][r] = e^{-2πi kr/16}
+ * (inverse = 1: e^{+2πi kr/16}), computed as BF16 hi/lo products
+ * accumulated in FP32 in tensor memory.  Synchronises `stream`.  Returns
+ * PSOLVE_ERR_TIMEOUT if the tensor-core completion wait ran out. */
+psolve_status psolve_debug_tc_dft16(const void *in, void *out, int nbutterflies, int inverse, void *stream);
+
 /* Static description of a status code. */
 const char *psolve_status_string(psolve_status s);
 

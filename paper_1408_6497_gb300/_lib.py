@@ -25,7 +25,8 @@ EXPORTS = ("psolve_plan_create", "psolve_plan_create_many", "psolve_execute", "p
            "psolve_execute_host", "psolve_destroy", "psolve_instance_offset",
            "psolve_total_elements", "psolve_get_status", "psolve_debug_kvec",
            "psolve_error_norms", "psolve_autotune", "psolve_set_profiling", "psolve_pass_times", "psolve_pass_name",
-           "psolve_launches_per_solve", "psolve_debug_set_wait", "psolve_execute_noalloc", "psolve_status_string",
+           "psolve_launches_per_solve", "psolve_debug_set_wait", "psolve_debug_tc_dft16",
+           "psolve_execute_noalloc", "psolve_status_string",
            "psolve_last_error", "psolve_version")
 
 
@@ -74,6 +75,7 @@ def load(path: str | None = None):
         lib.psolve_launches_per_solve.restype = i
         lib.psolve_execute_noalloc.argtypes = [i, i, i, i, vp, vp, vp]
         lib.psolve_debug_set_wait.argtypes = [vp, ctypes.c_ulonglong, i]
+        lib.psolve_debug_tc_dft16.argtypes = [vp, vp, i, i, vp]
         lib.psolve_status_string.argtypes = [i]
         lib.psolve_status_string.restype = ctypes.c_char_p
         lib.psolve_last_error.restype = ctypes.c_char_p

@@ -1,0 +1,221 @@
+// Radix-16 DFT stages on the 5th-generation tensor cores (tcgen05, sm_100+).
+//
+// A block of 128·G threads holds 128·G butterflies, thread tid the 16
+// complex inputs of butterfly (row) tid.  The stage computes, per row,
+//     b = F a,   F[k][r] = e^{∓2πi kr/16},
+// as the real product of the row [Re a | Im a] (32 values) with the 32×32
+// real form of F, [[Re F, -Im F], [Im F, Re F]], on the tensor cores:
+// operands in BF16 split as x = hi + lo (hi = bf16(x), lo = bf16(x - hi)),
+// accumulated in FP32 in tensor memory (TMEM) as hi·Fhi + hi·Flo + lo·Fhi
+// (the lo·lo term, ~2^-18 relative, is dropped).  Each thread reads its own
+// row of the accumulator back (tcgen05.ld 32x32b: warp w sees TMEM lanes
+// 32·(w mod 4) ..), so the outputs land where the FP32 butterfly would have
+// left them.
+//
+// Shared-memory operands use the no-swizzle K-major canonical layout: core
+// matrices of 8 rows × 16 bytes (8 BF16), 128 bytes each, K-adjacent core
+// matrices 128 B apart (leading byte offset) and 8-row groups 512 B apart
+// (stride byte offset) for K = 32.
+#pragma once
+
+#include <cuda_bf16.h>
+
+#include "fft_core.cuh"
+#include "tma.cuh"
+
+namespace psolve {
+
+constexpr int kTcK = 32;             // real K (16 complex inputs)
+constexpr int kTcN = 32;             // real N (16 complex outputs)
+constexpr int kTcRowBytes = kTcK * 2; // one BF16 row of A
+constexpr int kTcFBytes = kTcN * kTcRowBytes; // one 32×32 BF16 matrix (2 KiB)
+
+// Byte offset of element (row, k) of a K-major no-swizzle BF16 operand with K = 32.
+__host__ __device__ constexpr int tc_offset(int row, int k)
+{
+    return ((row >> 3) * 4 + (k >> 3)) * 128 + (row & 7) * 16 + (k & 7) * 2;
+}
+
+// Shared-memory matrix descriptor (tcgen05): start >> 4, leading byte offset
+// >> 4, stride byte offset >> 4, descriptor version 1, no swizzle.
+__device__ __forceinline__ uint64_t tc_smem_desc(const void *p, uint32_t lbo, uint32_t sbo)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((smem_u32(p) & 0x3FFFFu) >> 4);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;
+    return d;
+}
+
+// Instruction descriptor, kind::f16: D FP32, A and B BF16, both K-major,
+// N = 32, M = 128.
+constexpr uint32_t kTcIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kTcN >> 3) << 17) |
+                              ((uint32_t)(128 >> 4) << 24);
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// TMEM allocation by one full warp; the base address is written to *dst.
+__device__ __forceinline__ void tmem_alloc(uint32_t *dst, uint32_t ncols)
+{
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols)
+{
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t acc)
+{
+    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                 "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+                 "l"(adesc), "l"(bdesc), "r"(kTcIdesc), "r"(acc)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_commit(uint64_t *bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     smem_u32(bar))
+                 : "memory");
+}
+
+// 32 consecutive FP32 columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&r)[32])
+{
+    uint32_t u[32];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+                 "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                 "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                 : "=r"(u[0]), "=r"(u[1]), "=r"(u[2]), "=r"(u[3]), "=r"(u[4]), "=r"(u[5]), "=r"(u[6]),
+                   "=r"(u[7]), "=r"(u[8]), "=r"(u[9]), "=r"(u[10]), "=r"(u[11]), "=r"(u[12]), "=r"(u[13]),
+                   "=r"(u[14]), "=r"(u[15]), "=r"(u[16]), "=r"(u[17]), "=r"(u[18]), "=r"(u[19]),
+                   "=r"(u[20]), "=r"(u[21]), "=r"(u[22]), "=r"(u[23]), "=r"(u[24]), "=r"(u[25]),
+                   "=r"(u[26]), "=r"(u[27]), "=r"(u[28]), "=r"(u[29]), "=r"(u[30]), "=r"(u[31])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) r[i] = __uint_as_float(u[i]);
+}
+
+// Split x into BF16 hi + lo, packed two values per 32-bit word.
+__device__ __forceinline__ void bf16_split2(float x0, float x1, uint32_t &hi, uint32_t &lo)
+{
+    const __nv_bfloat16 h0 = __float2bfloat16_rn(x0), h1 = __float2bfloat16_rn(x1);
+    const __nv_bfloat16 l0 = __float2bfloat16_rn(x0 - __bfloat162float(h0));
+    const __nv_bfloat16 l1 = __float2bfloat16_rn(x1 - __bfloat162float(h1));
+    hi = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+    lo = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+}
+
+// Shared state of a block's tensor-core stages.
+struct TcCtx {
+    unsigned char *a_hi, *a_lo;   // 128·G rows × 64 B each
+    const unsigned char *f_hi[2]; // [forward, inverse] 32×32 BF16, hi part
+    const unsigned char *f_lo[2];
+    uint32_t tmem;                // TMEM base (32·G columns)
+    uint64_t *bar;                // MMA completion barrier
+    uint32_t *phase;              // completed MMA batches (shared counter)
+    int *abort;                   // shared flag set on a timed-out wait
+    int *status;                  // device status word
+};
+
+// Build the four 32×32 BF16 DFT matrices (hi/lo × forward/inverse) in shared
+// memory, from FP64 sincospi; called by the whole block.
+__device__ __forceinline__ void tc_build_dft16(unsigned char *f_hi_fwd, unsigned char *f_lo_fwd,
+                                               unsigned char *f_hi_inv, unsigned char *f_lo_inv)
+{
+    for (int i = threadIdx.x; i < kTcN * kTcK; i += blockDim.x) {
+        const int n = i / kTcK, k = i % kTcK;
+        const int kn = n & 15, kr = k & 15;
+        double s, c;
+        sincospi(2.0 * (double)((kn * kr) & 15) / 16.0, &s, &c); // angle 2π kn kr / 16
+        for (int inv = 0; inv < 2; ++inv) {
+            const double fi = inv ? s : -s; // Im F = ∓ sin
+            double v;
+            if (n < 16 && k < 16) v = c;
+            else if (n < 16) v = -fi;
+            else if (k < 16) v = fi;
+            else v = c;
+            const float vf = (float)v;
+            const __nv_bfloat16 h = __float2bfloat16_rn(vf);
+            const __nv_bfloat16 l = __float2bfloat16_rn(vf - __bfloat162float(h));
+            unsigned char *hp = inv ? f_hi_inv : f_hi_fwd;
+            unsigned char *lp = inv ? f_lo_inv : f_lo_fwd;
+            *reinterpret_cast<__nv_bfloat16 *>(hp + tc_offset(n, k)) = h;
+            *reinterpret_cast<__nv_bfloat16 *>(lp + tc_offset(n, k)) = l;
+        }
+    }
+}
+
+// a[16] (this thread's butterfly) <- F a on the tensor cores.  All threads
+// of the block call it; blockDim.x must be a multiple of 128.
+template <bool INV>
+__device__ __forceinline__ void tc_dft16(float2 (&a)[16], const TcCtx &ctx)
+{
+    const int tid = threadIdx.x;
+    // 1. this row of A, split into BF16 hi/lo, four 16-byte chunks each
+    {
+        uint32_t hi[16], lo[16];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            bf16_split2(a[2 * i].x, a[2 * i + 1].x, hi[i], lo[i]);         // Re a
+            bf16_split2(a[2 * i].y, a[2 * i + 1].y, hi[8 + i], lo[8 + i]); // Im a
+        }
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int off = tc_offset(tid, 8 * c);
+            *reinterpret_cast<uint4 *>(ctx.a_hi + off) = make_uint4(hi[4 * c], hi[4 * c + 1], hi[4 * c + 2], hi[4 * c + 3]);
+            *reinterpret_cast<uint4 *>(ctx.a_lo + off) = make_uint4(lo[4 * c], lo[4 * c + 1], lo[4 * c + 2], lo[4 * c + 3]);
+        }
+    }
+    fence_proxy_async_smem(); // generic-proxy writes of A before the tensor core reads them
+    tc_fence_before();
+    __syncthreads();
+    const uint32_t ph = *ctx.phase;
+    if (tid == 0) {
+        tc_fence_after();
+        const int groups = blockDim.x >> 7;
+        const unsigned char *fh = ctx.f_hi[INV ? 1 : 0];
+        const unsigned char *fl = ctx.f_lo[INV ? 1 : 0];
+        for (int g = 0; g < groups; ++g) {
+            const uint32_t d = ctx.tmem + (uint32_t)(kTcN * g);
+#pragma unroll
+            for (int ks = 0; ks < 2; ++ks) {
+                const int kofs = ks * 256; // two core matrices of K per step
+                const uint64_t ah = tc_smem_desc(ctx.a_hi + g * 128 * kTcRowBytes + kofs, 128, 512);
+                const uint64_t al = tc_smem_desc(ctx.a_lo + g * 128 * kTcRowBytes + kofs, 128, 512);
+                const uint64_t bh = tc_smem_desc(fh + kofs, 128, 512);
+                const uint64_t bl = tc_smem_desc(fl + kofs, 128, 512);
+                tc_mma(d, ah, bh, ks > 0 ? 1u : 0u);
+                tc_mma(d, ah, bl, 1u);
+                tc_mma(d, al, bh, 1u);
+            }
+        }
+        tc_commit(ctx.bar);
+        if (!mbar_wait_bounded(ctx.bar, ph & 1u, 2000000000ull)) {
+            *ctx.abort = 1;
+            atomicExch(ctx.status, 5 /* PSOLVE_ERR_TIMEOUT */);
+            mbar_wait_bounded(ctx.bar, ph & 1u, 2000000000ull); // let issued MMAs drain before TMEM is freed
+        }
+        *ctx.phase = ph + 1;
+    }
+    __syncthreads();
+    tc_fence_after();
+    if (*ctx.abort) return; // the caller checks ctx.abort too
+    // 2. this thread's accumulator row: columns 0..15 real, 16..31 imaginary
+    const int w = tid >> 5;
+    const uint32_t taddr = ctx.tmem + ((uint32_t)(32 * (w & 3)) << 16) + (uint32_t)(kTcN * (w >> 2));
+    float r[32];
+    tmem_ld32(taddr, r);
+#pragma unroll
+    for (int k = 0; k < 16; ++k) a[k] = make_float2(r[k], r[16 + k]);
+    tc_fence_before(); // these reads precede the next batch of MMAs
+}
+
+} // namespace psolve

@@ -21,7 +21,7 @@ def lib():
 
 def declared_symbols():
     text = open(HEADER).read()
-    return sorted(set(re.findall(r"\b(psolve_[a-z_]+)\s*\(", text)))
+    return sorted(set(re.findall(r"\b(psolve_[a-z_0-9]+)\s*\(", text)))
 
 
 def test_every_declared_symbol_is_exported(lib):
