@@ -42,7 +42,12 @@ extern "C" {
 typedef enum {
     PSOLVE_F64 = 0,     /* double in, double out, FP64 butterflies          */
     PSOLVE_F32 = 1,     /* float in, float out, FP32 butterflies            */
-    PSOLVE_F32_TC = 2   /* float in/out; radix-16 stages on tensor cores     */
+    PSOLVE_F32_TC = 2   /* float in/out; radix-16 stages of the y and x passes on the tensor
+                           cores (tcgen05, BF16 hi/lo operands, FP32 accumulation in TMEM)
+                           where those passes use the TMA kernels (lines of 256, 512 or 1024
+                           points); every other stage in FP32.  psolve_pass_name reports
+                           "yfwd_tc", "xdiv_tc", "yinv_tc" for the passes that do.  Equal-grid
+                           plans only. */
 } psolve_dtype;
 
 typedef enum {

@@ -749,6 +749,7 @@ psolve_status run_tma_pass(const psolve_plan *p, const Group &g, T *ui, int kind
         a.tw = reinterpret_cast<const float2 *>(p->tables) + (kind == 2 ? g.tw_x : g.tw_y);
         a.coef = (float)(1.0 / (4.0 * M_PI * M_PI * ((double)g.nx * g.ny * g.nz)));
         a.status = p->status;
+        a.tc = p->dtype == PSOLVE_F32_TC ? 1 : 0;
         if (narrow == 2 && kind == 2 && !make_line_plan_E(g.nx, 8, a.pl_x))
             return fail(PSOLVE_ERR_INTERNAL, "no 8-point plan for the x line");
         long long work = a.main_tiles;
@@ -1104,8 +1105,6 @@ psolve_status psolve_plan_create(int nx, int ny, int nz, int dtype, int batch, p
     *out = nullptr;
     if (dtype != PSOLVE_F64 && dtype != PSOLVE_F32 && dtype != PSOLVE_F32_TC)
         return fail(PSOLVE_ERR_INVALID_ARG, "unknown dtype");
-    if (dtype == PSOLVE_F32_TC)
-        return fail(PSOLVE_ERR_INVALID_ARG, "tensor-core precision is not built in this version");
     if (batch < 1) return fail(PSOLVE_ERR_INVALID_ARG, "batch must be >= 1");
     if (!size_ok(nx) || !size_ok(ny) || !size_ok(nz))
         return fail(PSOLVE_ERR_UNSUPPORTED_SIZE, "each n must be 2^a 3^b, even, 4 <= n <= 2048");
@@ -1122,7 +1121,7 @@ psolve_status psolve_plan_create_many(const int *nx, const int *ny, const int *n
     if (dtype != PSOLVE_F64 && dtype != PSOLVE_F32 && dtype != PSOLVE_F32_TC)
         return fail(PSOLVE_ERR_INVALID_ARG, "unknown dtype");
     if (dtype == PSOLVE_F32_TC)
-        return fail(PSOLVE_ERR_INVALID_ARG, "tensor-core precision is not built in this version");
+        return fail(PSOLVE_ERR_INVALID_ARG, "tensor-core precision applies to plans of equal grids");
     if (batch < 1) return fail(PSOLVE_ERR_INVALID_ARG, "batch must be >= 1");
     std::vector<int> X(nx, nx + batch), Y(ny, ny + batch), Z(nz, nz + batch);
     for (int b = 0; b < batch; ++b)
@@ -1299,6 +1298,11 @@ const char *psolve_pass_name(const psolve_plan *plan, int i)
 {
     if (!plan_ok(plan) || i < 0 || i >= kPasses) return nullptr;
     if (plan->batched) return i == 0 ? "batched" : "none";
+    if (plan->dtype == PSOLVE_F32_TC) {
+        const Group &g = plan->groups[0];
+        if ((i == 1 || i == 3) && g.cfg_y >= 0) return i == 1 ? "yfwd_tc" : "yinv_tc";
+        if (i == 2 && g.cfg_x >= 0) return "xdiv_tc";
+    }
     return kPassNames[i];
 }
 

@@ -38,6 +38,7 @@ struct TmaArgs {
     float coef;            // 1 / (4π² N)
     int *status;           // device status word
     LinePlan pl_x;         // run-time plan of the x line (packed-column pairs)
+    int tc;                // radix-16 stages on the tensor cores (cfg 0 and 1 only)
 };
 bool tma_supported(int L);
 // cfg 0: 64 KiB tiles, 16 points per thread, one 512-thread block per SM;

@@ -13,6 +13,7 @@
 #include "psolve.h"
 #include "launch.h"
 #include "tma.cuh"
+#include "tc.cuh"
 
 namespace psolve {
 
@@ -39,12 +40,16 @@ template <int L, int CFG> struct TmaShape {
 };
 
 // KIND: 0 = y forward, 1 = y inverse, 2 = x forward + division + x inverse.
-template <int L, int KIND, int CFG>
+// TC: radix-16 stages on the tensor cores (BF16 hi/lo, FP32 accumulation in
+// TMEM); the exchange buffer then holds the BF16 operand rows instead (it
+// has exactly their size: one 128-byte row per thread).
+template <int L, int KIND, int CFG, bool TC>
 __global__ void __launch_bounds__(TmaShape<L, CFG>::NT, TmaShape<L, CFG>::MINB)
     k_strided_tma(const __grid_constant__ CUtensorMap tmap, TmaArgs a)
 {
     using S = TmaShape<L, CFG>;
     constexpr int E = S::E, TL = S::TL, W = S::W;
+    static_assert(!TC || (E == 16 && S::NT % 128 == 0), "tensor-core stages need 16 points per thread");
     extern __shared__ __align__(128) unsigned char smraw[];
     float2 *buf0 = reinterpret_cast<float2 *>(smraw);
     float2 *buf1 = buf0 + L * W;
@@ -52,6 +57,12 @@ __global__ void __launch_bounds__(TmaShape<L, CFG>::NT, TmaShape<L, CFG>::MINB)
     float2 *stw = xbuf + L * W;
     uint64_t *bar = reinterpret_cast<uint64_t *>(stw + L);
     int *abort_flag = reinterpret_cast<int *>(bar + 2);
+    // tensor-core state after the FP32 layout: MMA barrier, counters, DFT matrices
+    uint64_t *mbar = bar + 4;
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(mbar + 1);
+    uint32_t *tphase = tslot + 1;
+    unsigned char *fmat = reinterpret_cast<unsigned char *>(bar + 8);
+    constexpr uint32_t kCols = 32 * (S::NT / 128);
 
     const int tid = threadIdx.x;
     const int w = tid % W, t = tid / W;
@@ -61,11 +72,35 @@ __global__ void __launch_bounds__(TmaShape<L, CFG>::NT, TmaShape<L, CFG>::MINB)
         mbar_init(&bar[0], 1);
         mbar_init(&bar[1], 1);
         *abort_flag = 0;
+        if constexpr (TC) {
+            mbar_init(mbar, 1);
+            *tphase = 0;
+        }
         fence_mbar_init();
         tma_prefetch_desc(&tmap);
     }
     for (int i = tid; i < L; i += blockDim.x) stw[i] = a.tw[i];
+    TcCtx tc{};
+    if constexpr (TC) {
+        tc_build_dft16(fmat, fmat + kTcFBytes, fmat + 2 * kTcFBytes, fmat + 3 * kTcFBytes);
+        if (tid < 32) tmem_alloc(tslot, kCols);
+        tc_fence_before();
+    }
     __syncthreads();
+    if constexpr (TC) {
+        tc_fence_after();
+        tc.a_hi = reinterpret_cast<unsigned char *>(xbuf);
+        tc.a_lo = tc.a_hi + S::NT * kTcRowBytes;
+        tc.f_hi[0] = fmat;
+        tc.f_lo[0] = fmat + kTcFBytes;
+        tc.f_hi[1] = fmat + 2 * kTcFBytes;
+        tc.f_lo[1] = fmat + 3 * kTcFBytes;
+        tc.tmem = *tslot;
+        tc.bar = mbar;
+        tc.phase = tphase;
+        tc.abort = abort_flag;
+        tc.status = a.status;
+    }
 
     // Tile -> TMA coordinates (c0 = first column, c1, c2 of the first row).
     auto issue = [&](long long tile, float2 *dst, uint64_t *b) {
@@ -106,7 +141,7 @@ __global__ void __launch_bounds__(TmaShape<L, CFG>::NT, TmaShape<L, CFG>::MINB)
             }
         }
         __syncthreads();
-        if (*abort_flag) return;
+        if (*abort_flag) break;
 
         const int cb = (int)(tile % a.ncb);
         const long long rest = tile / a.ncb;
@@ -115,9 +150,15 @@ __global__ void __launch_bounds__(TmaShape<L, CFG>::NT, TmaShape<L, CFG>::MINB)
         float2 v[E];
 #pragma unroll
         for (int m = 0; m < E; ++m) v[m] = cur[(t + m * TL) * W + w];
-        // Exchanges alternate xbuf, cur, xbuf, ...: the first writes go to
-        // xbuf, so the tile reads above need no barrier of their own.
-        line_fft_ct_db<KIND == 1, L, 0, 0>(v, t, stw, xbuf, cur, map);
+        if constexpr (TC) {
+            __syncthreads(); // single-buffer exchanges in `cur`
+            line_fft_tc_from<KIND == 1, L, 0>(v, t, stw, cur, map, tc);
+            if (*abort_flag) break;
+        } else {
+            // Exchanges alternate xbuf, cur, xbuf, ...: the first writes go to
+            // xbuf, so the tile reads above need no barrier of their own.
+            line_fft_ct_db<KIND == 1, L, 0, 0>(v, t, stw, xbuf, cur, map);
+        }
 
         float2 *base;
         long long step;
@@ -134,9 +175,14 @@ __global__ void __launch_bounds__(TmaShape<L, CFG>::NT, TmaShape<L, CFG>::MINB)
                 const float d = (k2 == 0) ? 0.f : __fdividef(a.coef, (float)k2);
                 v[m] = cscale(v[m], d);
             }
-            // Continue the alternation where the forward transform left it.
-            constexpr int PAR = ct_exchanges(L, E) & 1;
-            line_fft_ct_db<true, L, 0, PAR>(v, t, stw, xbuf, cur, map);
+            if constexpr (TC) {
+                line_fft_tc_from<true, L, 0>(v, t, stw, cur, map, tc);
+                if (*abort_flag) break;
+            } else {
+                // Continue the alternation where the forward transform left it.
+                constexpr int PAR = ct_exchanges(L, E) & 1;
+                line_fft_ct_db<true, L, 0, PAR>(v, t, stw, xbuf, cur, map);
+            }
             step = (long long)TL * a.ny * a.M;
             base = a.data + inst * a.sInst + (long long)y * a.M + col + (long long)t * a.ny * a.M;
         } else {
@@ -150,7 +196,7 @@ __global__ void __launch_bounds__(TmaShape<L, CFG>::NT, TmaShape<L, CFG>::MINB)
         __syncthreads(); // `cur` is free for the copy issued next iteration
     }
 
-    if (KIND == 2) {
+    if (KIND == 2 && !*abort_flag) {
         // Packed column pairs, one group of W/2 pairs per block-iteration.
         const long long npt = (a.npairs + W / 2 - 1) / (W / 2);
         for (long long p = blockIdx.x; p < npt; p += gridDim.x) {
@@ -159,14 +205,22 @@ __global__ void __launch_bounds__(TmaShape<L, CFG>::NT, TmaShape<L, CFG>::MINB)
             __syncthreads();
         }
     }
+    if constexpr (TC) {
+        tc_fence_before();
+        __syncthreads();
+        if (tid < 32) {
+            tc_fence_after();
+            tmem_dealloc(tc.tmem, kCols);
+        }
+    }
 }
 
-template <int L, int KIND, int CFG>
+template <int L, int KIND, int CFG, bool TC>
 cudaError_t run(const CUtensorMap &map, const TmaArgs &a, unsigned grid, cudaStream_t s)
 {
     using S = TmaShape<L, CFG>;
-    const size_t smem = tma_smem_bytes(L, S::NARROW);
-    auto kern = k_strided_tma<L, KIND, CFG>;
+    const size_t smem = tma_smem_bytes(L, S::NARROW) + (TC ? 64 + 4 * kTcFBytes : 0);
+    auto kern = k_strided_tma<L, KIND, CFG, TC>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     kern<<<grid, S::NT, smem, s>>>(map, a);
@@ -186,10 +240,29 @@ bool tma_supported(int L) { return L == 256 || L == 512 || L == 1024; }
 cudaError_t launch_strided_tma(const CUtensorMap &map, const TmaArgs &a, int L, int kind, int cfg,
                                unsigned grid, cudaStream_t s)
 {
+    if (a.tc) {
+        if (cfg == 2) return cudaErrorInvalidValue;
+#define PSOLVE_TMA_TC(LL)                                                               \
+        if (L == LL) {                                                                  \
+            if (cfg == 1) {                                                             \
+                if (kind == 0) return run<LL, 0, 1, true>(map, a, grid, s);             \
+                if (kind == 1) return run<LL, 1, 1, true>(map, a, grid, s);             \
+                return run<LL, 2, 1, true>(map, a, grid, s);                            \
+            }                                                                           \
+            if (kind == 0) return run<LL, 0, 0, true>(map, a, grid, s);                 \
+            if (kind == 1) return run<LL, 1, 0, true>(map, a, grid, s);                 \
+            return run<LL, 2, 0, true>(map, a, grid, s);                                \
+        }
+        PSOLVE_TMA_TC(256)
+        PSOLVE_TMA_TC(512)
+        PSOLVE_TMA_TC(1024)
+#undef PSOLVE_TMA_TC
+        return cudaErrorInvalidValue;
+    }
 #define PSOLVE_TMA_KIND(LL, CF)                                                         \
-    if (kind == 0) return run<LL, 0, CF>(map, a, grid, s);                              \
-    if (kind == 1) return run<LL, 1, CF>(map, a, grid, s);                              \
-    return run<LL, 2, CF>(map, a, grid, s);
+    if (kind == 0) return run<LL, 0, CF, false>(map, a, grid, s);                       \
+    if (kind == 1) return run<LL, 1, CF, false>(map, a, grid, s);                       \
+    return run<LL, 2, CF, false>(map, a, grid, s);
 #define PSOLVE_TMA_CASE(LL)                                                             \
     case LL:                                                                            \
         if (cfg == 2) { PSOLVE_TMA_KIND(LL, 2) }                                        \

@@ -218,4 +218,50 @@ __device__ __forceinline__ void tc_dft16(float2 (&a)[16], const TcCtx &ctx)
     tc_fence_before(); // these reads precede the next batch of MMAs
 }
 
+// Compile-time-plan line transform in which every radix-16 stage runs on the
+// tensor cores (E = 16: one butterfly per thread and stage).  Twiddles and
+// other radices stay in FP32.  Single-buffer exchanges in `sm`.  All threads
+// of the block call it; on a timed-out tensor-core wait it returns early
+// with *ctx.abort set (uniformly across the block).
+template <bool INV, int L, int S, typename Map>
+__device__ __forceinline__ void line_fft_tc_from(float2 (&v)[16], int t, const float2 *__restrict__ tw,
+                                                 float2 *sm, const Map &map, const TcCtx &ctx)
+{
+    constexpr int E = 16;
+    constexpr int NST = ct_nst(L, E);
+    if constexpr (S < NST) {
+        constexpr int R = ct_radix(L, S, E);
+        constexpr int NS = ct_ns(L, S, E);
+        constexpr int TL = L / E;
+        constexpr bool LAST = (S + 1 == NST);
+        if constexpr (R == 16) {
+            const int jm = t % NS;
+            if constexpr (NS > 1) {
+                const int q = jm * (L / (NS * 16));
+#pragma unroll
+                for (int r = 1; r < 16; ++r) {
+                    const float2 w = tw[r * q];
+                    v[r] = INV ? cmulc(v[r], w) : cmul(v[r], w);
+                }
+            }
+            tc_dft16<INV>(v, ctx);
+            if (*ctx.abort) return;
+            if constexpr (!LAST) {
+                const int base = (t - jm) * 16 + jm;
+#pragma unroll
+                for (int k = 0; k < 16; ++k) sm[map(base + k * NS)] = v[k];
+            }
+        } else {
+            fft_stage_ct<R, INV, LAST, TL, NS, L / (NS * R)>(v, t, tw, sm, map, true);
+        }
+        if constexpr (!LAST) {
+            __syncthreads();
+#pragma unroll
+            for (int m = 0; m < E; ++m) v[m] = sm[map(t + m * TL)];
+            __syncthreads();
+            line_fft_tc_from<INV, L, S + 1>(v, t, tw, sm, map, ctx);
+        }
+    }
+}
+
 } // namespace psolve

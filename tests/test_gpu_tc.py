@@ -34,3 +34,43 @@ def test_tc_dft16_matches_reference(lib, nb, inverse):
     # BF16 hi/lo operands, FP32 accumulation: ~2^-18 per product
     assert err < 1e-5, err
     assert err > 1e-9  # it really went through BF16 (not an FP32 copy)
+
+
+# ---------------------------------------------------------------- solves
+import oracle  # noqa: E402
+from paper_1408_6497_gb300 import Plan  # noqa: E402
+from paper_1408_6497_gb300 import workloads as wl  # noqa: E402
+
+
+def _solve(shape, prec, f64):
+    plan = Plan(shape, dtype=prec)
+    f = torch.from_numpy(f64.astype(np.float32).ravel()).cuda()
+    u = plan.execute(f)
+    plan.status()
+    names = [plan.lib.psolve_pass_name(plan.handle, i).decode() for i in range(5)]
+    return u.cpu().numpy().reshape(shape), f.cpu().numpy().reshape(shape), names
+
+
+@pytest.mark.parametrize("shape", [(256, 256, 64), (512, 256, 32), (256, 1024, 32), (1024, 256, 64)])
+def test_tc_solve_parity(lib, shape):
+    oracle.build()
+    f64 = wl.random_field(shape, seed=700 + sum(shape))
+    u, f_in, names = _solve(shape, "f32_tc", f64)
+    assert "yfwd_tc" in names and "xdiv_tc" in names and "yinv_tc" in names
+    err = oracle.rel_l2(u, oracle.solve(f_in.astype(np.float64)))
+    assert err <= 1e-5, (shape, err)
+
+
+def test_tc_solve_512_sharp_source_vs_oracle_and_fp32(lib):
+    """The tensor-core workload: 512^3 sharp source, rel-L2 <= 1e-5 against
+    the FP64 oracle, reported next to the plain FP32 path's error."""
+    oracle.build()
+    shape = (512, 512, 512)
+    w = wl.sharp_source(shape)
+    u_tc, f_in, names = _solve(shape, "f32_tc", w.f)
+    u_32, _, _ = _solve(shape, "f32", w.f)
+    ref = oracle.solve(f_in.astype(np.float64))
+    e_tc, e_32 = oracle.rel_l2(u_tc, ref), oracle.rel_l2(u_32, ref)
+    print(f"512^3 sharp source rel-L2: tensor-core {e_tc:.3e}, FP32 {e_32:.3e}; passes {names}")
+    assert e_tc <= 1e-5
+    assert e_32 <= 5e-6
