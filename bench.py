@@ -45,6 +45,11 @@ def parse():
     ap.add_argument("--workload", choices=["sharp", "batch64"], default="sharp",
                     help="sharp: one FP32 grid^3 solve per step (default, 512^3); batch64: the 64 "
                          "uneven radix-2/3 grids in one persistent launch per step")
+    ap.add_argument("--precision", choices=["f32", "f32_tc"], default="f32",
+                    help="f32: FP32 butterflies; f32_tc: radix-16 stages of the y/x passes on the "
+                         "tensor cores (BF16 hi/lo, FP32 accumulation)")
+    ap.add_argument("--check", action="store_true",
+                    help="also report this run's rel-L2 against the FP64 oracle (a few s of CPU)")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -237,7 +242,7 @@ def run_ours(args):
     u_pin = torch.empty_like(f_pin).pin_memory()
     f = f_pin.to(dev)
     u = torch.empty_like(f)
-    plan = Plan(shape, dtype="f32", device=dev)
+    plan = Plan(shape, dtype=args.precision, device=dev)
     if not args.no_autotune:
         plan.autotune()
     stream = torch.cuda.current_stream(dev)
@@ -304,9 +309,10 @@ def run_ours(args):
     line = {
         "impl": "ours", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if args.precision == "f32" else "f32+bf16x3-tc",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "grid": list(shape), "precision": "f32",
+        "config": {"workload": WORKLOAD, "grid": list(shape), "precision": args.precision,
                    "l2": "inputs larger than L2 (512 MiB f and u), no flush",
                    "parallelism": "replicas" if ws > 1 else "single GPU",
                    "clock_window": "2 s soak + timed region"},
@@ -321,6 +327,12 @@ def run_ours(args):
         "gpu_launches": plan.launches_per_solve * args.steps,
         "clocks": clocks,
     }
+    if args.check and rank == 0:
+        import oracle
+        from paper_1408_6497_gb300 import workloads as wl2
+        plan.execute(f, u)
+        ref = oracle.solve(wl2.sharp_source(shape).f.astype(np.float32).astype(np.float64))
+        line["rel_l2_vs_oracle"] = oracle.rel_l2(u.cpu().numpy().reshape(shape), ref)
     if ws == 1 and not args.no_cpu_baseline:
         rate, t, reps, cores = oracle_rate(min(n, 256), max_seconds=20.0)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",

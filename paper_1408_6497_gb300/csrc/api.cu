@@ -415,8 +415,8 @@ void apply_tuning_cache(psolve_plan *p)
         it = m.find(tune_key(p, path, 'y', g.ny, g.M));
         if (it != m.end()) {
             const TuneChoice c = it->second;
-            if (c.cfg >= 0 && tma_fits(p, g.ny, g.M, c.cfg)) g.cfg_y = c.cfg;
-            else if (c.cfg < 0 && c.W >= 1 && c.W <= g.M && c.W * g.py.TL <= max_threads(fp64, g.py.E) &&
+            if (c.cfg >= 0 && tma_fits(p, g.ny, g.M, c.cfg) && !(p->dtype == PSOLVE_F32_TC && c.cfg > 1)) g.cfg_y = c.cfg;
+            else if (c.cfg < 0 && !(p->dtype == PSOLVE_F32_TC && g.cfg_y >= 0) && c.W >= 1 && c.W <= g.M && c.W * g.py.TL <= max_threads(fp64, g.py.E) &&
                      s_smem(g.ny, c.W, p->dtype) <= kSmemCap) {
                 g.cfg_y = -1;
                 g.Wy = c.W;
@@ -425,8 +425,8 @@ void apply_tuning_cache(psolve_plan *p)
         it = m.find(tune_key(p, path, 'x', g.nx, g.M));
         if (it != m.end()) {
             const TuneChoice c = it->second;
-            if (c.cfg >= 0 && tma_fits(p, g.nx, g.M, c.cfg)) g.cfg_x = c.cfg;
-            else if (c.cfg < 0 && c.W >= 2 && c.W * g.px.TL <= max_threads(fp64, g.px.E) &&
+            if (c.cfg >= 0 && tma_fits(p, g.nx, g.M, c.cfg) && !(p->dtype == PSOLVE_F32_TC && c.cfg > 1)) g.cfg_x = c.cfg;
+            else if (c.cfg < 0 && !(p->dtype == PSOLVE_F32_TC && g.cfg_x >= 0) && c.W >= 2 && c.W * g.px.TL <= max_threads(fp64, g.px.E) &&
                      s_smem(g.nx, c.W, p->dtype) <= kSmemCap) {
                 g.cfg_x = -1;
                 g.Wx = c.W;
@@ -1060,7 +1060,10 @@ template <typename T> psolve_status autotune_impl(psolve_plan *p, cudaStream_t s
                 const LinePlan &pl = axis == 0 ? g.py : g.px;
                 float bt = inf;
                 int bcfg = -1, bW = axis == 0 ? g.Wy : g.Wx;
-                for (int cfg = 0; cfg < 3 && !fp64; ++cfg) {
+                // A tensor-core plan keeps its passes on the tensor cores: only
+                // the TMA configurations with tensor-core variants (0, 1) compete.
+                const bool tc = p->dtype == PSOLVE_F32_TC;
+                for (int cfg = 0; cfg < (tc ? 2 : 3) && !fp64; ++cfg) {
                     if (!tma_fits(p, L, g.M, cfg)) continue;
                     if (axis == 0) gt.cfg_y = cfg; else gt.cfg_x = cfg;
                     const float t = timed(gt, kind, false);
@@ -1068,6 +1071,7 @@ template <typename T> psolve_status autotune_impl(psolve_plan *p, cudaStream_t s
                 }
                 if (axis == 0) gt.cfg_y = -1; else gt.cfg_x = -1;
                 for (int W : wlist) {
+                    if (tc && bcfg >= 0) break;
                     if (W < (axis == 0 ? 1 : 2) || (axis == 0 && W > g.M) || W * pl.TL > max_threads(fp64, pl.E) ||
                         s_smem(L, W, p->dtype) > kSmemCap)
                         continue;

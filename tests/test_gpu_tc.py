@@ -74,3 +74,18 @@ def test_tc_solve_512_sharp_source_vs_oracle_and_fp32(lib):
     print(f"512^3 sharp source rel-L2: tensor-core {e_tc:.3e}, FP32 {e_32:.3e}; passes {names}")
     assert e_tc <= 1e-5
     assert e_32 <= 5e-6
+
+
+def test_tc_plan_stays_on_tensor_cores_after_autotune(lib, tmp_path, monkeypatch):
+    monkeypatch.setenv("PSOLVE_TUNE_CACHE", str(tmp_path / "tune.txt"))
+    oracle.build()
+    shape = (256, 512, 64)
+    plan = Plan(shape, dtype="f32_tc")
+    plan.autotune()
+    names = [plan.lib.psolve_pass_name(plan.handle, i).decode() for i in range(5)]
+    assert names == ["zfwd", "yfwd_tc", "xdiv_tc", "yinv_tc", "zinv"]
+    f64 = wl.random_field(shape, seed=3)
+    f = torch.from_numpy(f64.astype(np.float32).ravel()).cuda()
+    u = plan.execute(f).cpu().numpy().reshape(shape)
+    err = oracle.rel_l2(u, oracle.solve(f.cpu().numpy().astype(np.float64).reshape(shape)))
+    assert 1e-7 < err <= 1e-5  # tensor-core accuracy, not an FP32 result
