@@ -50,6 +50,7 @@ struct Group {
     size_t tw_z, tw_y, tw_x, post; // complex-element offsets into the table buffer
     int Wz, Wy, Wx;
     int cfg_y, cfg_x;    // TMA configuration of the y / x pass (-1: per-tile kernel)
+    int fused;           // z and y passes fused per plane through L2: cluster size, 0 = off
 };
 
 bool factor23(int n, int &a, int &b)
@@ -412,6 +413,10 @@ void apply_tuning_cache(psolve_plan *p)
             g.Wz = it->second.W;
             if (g.Wz * g.pz.TL > max_threads(fp64, g.pz.E) || z_smem(g, p->dtype) > kSmemCap) g.Wz = keep;
         }
+        it = m.find(tune_key(p, path, 'f', g.ny, g.M));
+        if (it != m.end() && p->dtype == PSOLVE_F32 && fused_supported(g.M, g.ny) && g.pz.E == 16 &&
+            g.py.E == 16 && (it->second.W == 0 || it->second.W == 2 || it->second.W == 4 || it->second.W == 8))
+            g.fused = it->second.W;
         it = m.find(tune_key(p, path, 'y', g.ny, g.M));
         if (it != m.end()) {
             const TuneChoice c = it->second;
@@ -636,6 +641,14 @@ psolve_status build_plan(const std::vector<int> &nx, const std::vector<int> &ny,
         }
     }
     for (auto &g : p->groups) {
+        g.fused = 0;
+        if (uniform && dtype == PSOLVE_F32 && fused_supported(g.M, g.ny) && g.pz.E == 16 && g.py.E == 16) {
+            // Off by default (measured slower than the separate TMA passes on
+            // GB300 at 512^3 and 1024^3); the autotuner times it.
+            const char *fe = std::getenv("PSOLVE_FUSED");
+            g.fused = 0;
+            if (fe && fe[0] >= '1' && fe[0] <= '8') g.fused = fe[0] - '0';
+        }
         g.cfg_y = tma_fits(p.get(), g.ny, g.M, tma_variant(p->tma_narrow_y, g.ny))
                       ? tma_variant(p->tma_narrow_y, g.ny) : -1;
         g.cfg_x = tma_fits(p.get(), g.nx, g.M, tma_variant(p->tma_narrow_x, g.nx))
@@ -832,6 +845,49 @@ psolve_status launch_pass(const psolve_plan *p, const Group &g, int kind, const 
     return PSOLVE_OK;
 }
 
+// z+y (forward) or y+z (inverse) of every plane in one cluster launch.
+template <typename T>
+psolve_status launch_fused(const psolve_plan *p, const Group &g, bool inverse, const T *fi, T *ui, cudaStream_t s)
+{
+    if constexpr (sizeof(T) != 4) {
+        return fail(PSOLVE_ERR_INTERNAL, "fused z/y passes are FP32 only");
+    } else {
+        using C = float2;
+        const C *tab = reinterpret_cast<const C *>(p->tables);
+        const int NT = kFusedThreads;
+        ZArgs<float> z{};
+        z.in = inverse ? ui : fi;
+        z.out = ui;
+        z.rows = (long long)g.count * g.nx * g.ny;
+        z.nz = g.nz;
+        z.M = g.M;
+        z.W = NT / g.pz.TL;
+        z.pl = g.pz;
+        z.tw = tab + g.tw_z;
+        z.post = tab + g.post;
+        SArgs<float> y{};
+        y.data = ui;
+        y.nplanes = (long long)g.count * g.nx;
+        y.sPlane = (long long)g.ny * g.M;
+        y.sL = g.M;
+        y.M = g.M;
+        y.W = std::min(g.M, NT / g.py.TL);
+        y.ncb = (g.M + y.W - 1) / y.W;
+        y.pl = g.py;
+        y.tw = tab + g.tw_y;
+        FusedArgs fa{};
+        fa.planes = (long long)g.count * g.nx;
+        fa.cluster = g.fused;
+        fa.ztiles = g.ny / z.W;
+        fa.ytiles = y.ncb;
+        const size_t smem = std::max((size_t)(g.M + (size_t)z.W * zpitch(g.M)) * sizeof(C),
+                                     s_smem(g.ny, y.W, p->dtype));
+        cudaError_t e = launch_fused_zy(z, y, fa, inverse, smem, s);
+        if (e != cudaSuccess) return cuda_fail(e, inverse ? "fused y/z inverse pass" : "fused z/y forward pass");
+        return PSOLVE_OK;
+    }
+}
+
 template <typename T>
 psolve_status run_group(const psolve_plan *p, const Group &g, const T *f, T *u, cudaStream_t s,
                         const std::vector<cudaEvent_t> *ev)
@@ -839,6 +895,22 @@ psolve_status run_group(const psolve_plan *p, const Group &g, const T *f, T *u, 
     const T *fi = f + g.off0;
     T *ui = u + g.off0;
     if (ev) cudaEventRecord((*ev)[0], s);
+    if (g.fused > 0) {
+        psolve_status st = launch_fused<T>(p, g, false, fi, ui, s);
+        if (st != PSOLVE_OK) return st;
+        if (ev) cudaEventRecord((*ev)[1], s);
+        st = launch_pass<T>(p, g, 2, fi, ui, s);
+        if (st != PSOLVE_OK) return st;
+        if (ev) cudaEventRecord((*ev)[2], s);
+        st = launch_fused<T>(p, g, true, fi, ui, s);
+        if (st != PSOLVE_OK) return st;
+        if (ev) {
+            cudaEventRecord((*ev)[3], s);
+            cudaEventRecord((*ev)[4], s);
+            cudaEventRecord((*ev)[5], s);
+        }
+        return PSOLVE_OK;
+    }
     for (int kind = 0; kind < kPasses; ++kind) {
         psolve_status st = launch_pass<T>(p, g, kind, fi, ui, s);
         if (st != PSOLVE_OK) return st;
@@ -1083,6 +1155,24 @@ template <typename T> psolve_status autotune_impl(psolve_plan *p, cudaStream_t s
                 else { g.cfg_x = gt.cfg_x = bcfg; g.Wx = gt.Wx = bW; }
                 cache[tune_key(p, "pass", axis == 0 ? 'y' : 'x', L, g.M)] = TuneChoice{bW, bcfg, 0};
             }
+            // z/y fused through L2 against separate passes, timed as whole solves.
+            if (p->dtype == PSOLVE_F32 && fused_supported(g.M, g.ny) && g.pz.E == 16 && g.py.E == 16) {
+                float bt = inf;
+                int bf = 0;
+                for (int fz : {0, 4, 8}) {
+                    gt.fused = fz;
+                    if (run_group<T>(p, gt, buf, buf, s, nullptr) != PSOLVE_OK) continue;
+                    cudaEventRecord(e0, s);
+                    for (int r = 0; r < 3; ++r) run_group<T>(p, gt, buf, buf, s, nullptr);
+                    cudaEventRecord(e1, s);
+                    if (cudaEventSynchronize(e1) != cudaSuccess) continue;
+                    float ms = 0.f;
+                    cudaEventElapsedTime(&ms, e0, e1);
+                    if (ms / 3 < bt) { bt = ms / 3; bf = fz; }
+                }
+                g.fused = gt.fused = bf;
+                cache[tune_key(p, "pass", 'f', g.ny, g.M)] = TuneChoice{bf, -1, 0};
+            }
         }
     }
     cudaEventDestroy(e0);
@@ -1273,6 +1363,12 @@ psolve_status psolve_set_profiling(psolve_plan *plan, int enable)
     return PSOLVE_OK;
 }
 
+int plan_passes(const psolve_plan *p)
+{
+    if (p->batched) return 1;
+    return (p->groups.size() == 1 && p->groups[0].fused > 0) ? 3 : kPasses;
+}
+
 psolve_status psolve_pass_times(psolve_plan *plan, double *ms, int cap, int *n_passes, int *n_solves)
 {
     if (!plan_ok(plan)) return fail(PSOLVE_ERR_INVALID_ARG, "invalid or destroyed plan");
@@ -1293,7 +1389,7 @@ psolve_status psolve_pass_times(psolve_plan *plan, double *ms, int cap, int *n_p
     }
     for (auto &set : plan->ev_used) plan->ev_free.push_back(std::move(set));
     plan->ev_used.clear();
-    if (n_passes) *n_passes = kPasses;
+    if (n_passes) *n_passes = plan_passes(plan);
     if (n_solves) *n_solves = solves;
     return PSOLVE_OK;
 }
@@ -1302,6 +1398,10 @@ const char *psolve_pass_name(const psolve_plan *plan, int i)
 {
     if (!plan_ok(plan) || i < 0 || i >= kPasses) return nullptr;
     if (plan->batched) return i == 0 ? "batched" : "none";
+    if (plan_passes(plan) == 3) {
+        static const char *fused_names[3] = {"zyfwd", "xdiv", "yzinv"};
+        return i < 3 ? fused_names[i] : "none";
+    }
     if (plan->dtype == PSOLVE_F32_TC) {
         const Group &g = plan->groups[0];
         if ((i == 1 || i == 3) && g.cfg_y >= 0) return i == 1 ? "yfwd_tc" : "yinv_tc";
@@ -1314,7 +1414,7 @@ int psolve_launches_per_solve(const psolve_plan *plan)
 {
     if (!plan_ok(plan)) return 0;
     if (plan->batched) return 1;
-    return kPasses * (int)plan->groups.size();
+    return plan_passes(plan) * (int)plan->groups.size();
 }
 
 psolve_status psolve_debug_set_wait(psolve_plan *plan, unsigned long long wait_ns, int unsatisfiable)

@@ -51,6 +51,18 @@ size_t tma_smem_bytes(int L, int cfg);
 cudaError_t launch_strided_tma(const CUtensorMap &map, const TmaArgs &a, int L, int kind, int cfg,
                                unsigned grid, cudaStream_t s);
 
+// z and y passes of a plane fused through L2 in one cluster launch.
+constexpr int kFusedThreads = 256;
+struct FusedArgs {
+    long long planes; // x-planes (instances · nx)
+    int cluster;      // blocks per plane (cluster size)
+    int ztiles;       // row tiles per plane
+    int ytiles;       // column tiles per plane
+};
+bool fused_supported(int M, int ny);
+cudaError_t launch_fused_zy(const ZArgs<float> &az, const SArgs<float> &ay, const FusedArgs &fa, bool inverse,
+                            size_t smem, cudaStream_t s);
+
 // Persistent batched kernel: one segment per (pass, instance), pass-major.
 constexpr int kBatchThreads = 256;
 template <typename T> struct BatchSeg {

@@ -74,6 +74,38 @@ def test_tma_pass_batch_fp32():
         assert oracle.rel_l2(u[b], oracle.solve(f_in[b].astype(np.float64))) <= TOL["f32"]
 
 
+# z rows of 512/1024 points with y lines of 256/512/1024 points take the
+# fused z/y cluster passes in FP32 (one plane per cluster, L2 hand-off).
+FUSED_SHAPES = [(128, 256, 512), (64, 512, 1024), (32, 1024, 512), (48, 512, 512)]
+
+
+@pytest.mark.parametrize("shape", FUSED_SHAPES)
+def test_fused_zy_parity_fp32(shape, monkeypatch):
+    monkeypatch.setenv("PSOLVE_FUSED", "4")
+    f64 = wl.random_field(shape, seed=800 + sum(shape))
+    plan = Plan(shape, dtype="f32")
+    names = [plan.lib.psolve_pass_name(plan.handle, i).decode() for i in range(3)]
+    assert names == ["zyfwd", "xdiv", "yzinv"]
+    f = torch.from_numpy(f64.astype(np.float32).ravel()).cuda()
+    u = plan.execute(f)
+    plan.status()
+    ref = oracle.solve(f.cpu().numpy().astype(np.float64).reshape(shape))
+    err = oracle.rel_l2(u.cpu().numpy().reshape(shape), ref)
+    assert err <= TOL["f32"], (shape, err)
+    uu = f.clone()
+    plan.execute(uu, uu)  # in place
+    assert torch.equal(uu, u)
+
+
+def test_fused_zy_batch_fp32(monkeypatch):
+    monkeypatch.setenv("PSOLVE_FUSED", "4")
+    shape, B = (32, 256, 512), 3
+    f = np.stack([wl.random_field(shape, seed=90 + b) for b in range(B)])
+    u, f_in = gpu_solve(f, "f32", batch=B)
+    for b in range(B):
+        assert oracle.rel_l2(u[b], oracle.solve(f_in[b].astype(np.float64))) <= TOL["f32"]
+
+
 def test_config1_fp64_mode_sum_closed_form():
     w = wl.mode_sum()
     u, _ = gpu_solve(w.f, "f64")
