@@ -636,8 +636,8 @@ psolve_status build_plan(const std::vector<int> &nx, const std::vector<int> &ny,
         const char *nv = std::getenv("PSOLVE_TMA_NARROW");
         int ny_ = 0, nx_ = 0;
         if (nv && std::sscanf(nv, "%d,%d", &ny_, &nx_) == 2) {
-            p->tma_narrow_y = ny_ < 0 || ny_ > 2 ? 0 : ny_;
-            p->tma_narrow_x = nx_ < 0 || nx_ > 2 ? 0 : nx_;
+            p->tma_narrow_y = ny_ < 0 || ny_ > 3 ? 0 : ny_;
+            p->tma_narrow_x = nx_ < 0 || nx_ > 3 ? 0 : nx_;
         }
     }
     for (auto &g : p->groups) {
@@ -1135,7 +1135,7 @@ template <typename T> psolve_status autotune_impl(psolve_plan *p, cudaStream_t s
                 // A tensor-core plan keeps its passes on the tensor cores: only
                 // the TMA configurations with tensor-core variants (0, 1) compete.
                 const bool tc = p->dtype == PSOLVE_F32_TC;
-                for (int cfg = 0; cfg < (tc ? 2 : 3) && !fp64; ++cfg) {
+                for (int cfg = 0; cfg < (tc ? 2 : 4) && !fp64; ++cfg) {
                     if (!tma_fits(p, L, g.M, cfg)) continue;
                     if (axis == 0) gt.cfg_y = cfg; else gt.cfg_x = cfg;
                     const float t = timed(gt, kind, false);

@@ -179,6 +179,53 @@ template <bool INV, typename C> __device__ __forceinline__ void dft16(C *a)
     }
 }
 
+// Exact values of cos(πk/16), sin(πk/16) for odd k = 1, 3, 5, 7.
+struct Hex {
+    static constexpr double c[4] = {0.980785280403230449126182236134239037, 0.831469612302545237078788377617905757,
+                                    0.555570233019602224742830813948532874, 0.195090322016128267848284868477022241};
+};
+
+// a · w_32^k with w_32 = e^{∓2πi/32}, 0 <= k < 16.
+template <bool INV, int K, typename C> __device__ __forceinline__ C mul_w32(C a)
+{
+    using T = decltype(a.x);
+    if constexpr (K % 2 == 0) {
+        return mul_w16<INV, K / 2>(a);
+    } else {
+        // cos(πK/16), sin(πK/16) from the first octant: K = 1,3,5,7 direct,
+        // K = 9..15 via cos(π - x) = -cos x, sin(π - x) = sin x.
+        constexpr int k = K < 8 ? K : 16 - K;
+        const T c0 = (T)Hex::c[(k - 1) / 2];
+        const T s0 = (T)Hex::c[3 - (k - 1) / 2]; // sin(πk/16) = cos(π(8-k)/16)
+        const T c = K < 8 ? c0 : -c0;
+        const T s = INV ? s0 : -s0;
+        return C{a.x * c - a.y * s, a.x * s + a.y * c};
+    }
+}
+
+// 32 = 2 × 16 (decimation in time).
+template <bool INV, typename C> __device__ __forceinline__ void dft32(C *a)
+{
+    C e[16], o[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+        e[k] = a[2 * k];
+        o[k] = a[2 * k + 1];
+    }
+    dft16<INV>(e);
+    dft16<INV>(o);
+#define PSOLVE_R32(K)                                                                              \
+    {                                                                                              \
+        const C t = mul_w32<INV, K>(o[K]);                                                         \
+        a[K] = cadd(e[K], t);                                                                      \
+        a[K + 16] = csub(e[K], t);                                                                 \
+    }
+    PSOLVE_R32(0) PSOLVE_R32(1) PSOLVE_R32(2) PSOLVE_R32(3) PSOLVE_R32(4) PSOLVE_R32(5) PSOLVE_R32(6)
+    PSOLVE_R32(7) PSOLVE_R32(8) PSOLVE_R32(9) PSOLVE_R32(10) PSOLVE_R32(11) PSOLVE_R32(12) PSOLVE_R32(13)
+    PSOLVE_R32(14) PSOLVE_R32(15)
+#undef PSOLVE_R32
+}
+
 template <int R, bool INV, typename C> __device__ __forceinline__ void dft(C *a)
 {
     if constexpr (R == 2) dft2<INV>(a);
@@ -186,6 +233,7 @@ template <int R, bool INV, typename C> __device__ __forceinline__ void dft(C *a)
     else if constexpr (R == 4) dft4<INV>(a);
     else if constexpr (R == 8) dft8<INV>(a);
     else if constexpr (R == 16) dft16<INV>(a);
+    else if constexpr (R == 32) dft32<INV>(a);
 }
 
 // ------------------------------------------------------------------ plans
@@ -207,6 +255,12 @@ struct LinePlan {
 struct MapStrided { // [p][w], pitch P: lines side by side (y and x passes)
     int P, w;
     __device__ __forceinline__ int operator()(int p) const { return p * P + w; }
+};
+struct MapStridedPad { // [p][w] with a spare row after every 16 rows: the rows
+                       // 16 apart written together by the first Stockham stage
+                       // then fall in different banks (row step 17·P)
+    int P, w;
+    __device__ __forceinline__ int operator()(int p) const { return (p + (p >> 4)) * P + w; }
 };
 struct MapRow { // [w][p], one padded row per line (z passes)
     int base;
@@ -316,7 +370,7 @@ constexpr int ct_E(int L)
 {
     return ct_pow3(L) > 0 ? 3 * (1 << ct_min(ct_pow2(L), 3)) : (1 << ct_min(ct_pow2(L), 4));
 }
-constexpr int ct_p2(int E) { int p = 1; while (E % (p * 2) == 0 && p * 2 <= 16) p *= 2; return p; }
+constexpr int ct_p2(int E) { int p = 1; while (E % (p * 2) == 0 && p * 2 <= 32) p *= 2; return p; }
 constexpr int ct_radix(int L, int s, int E = 0)
 {
     const int b = ct_pow3(L);
@@ -401,13 +455,13 @@ __device__ __forceinline__ void line_fft_ct_from(C (&v)[E], int t, const C *__re
 }
 
 // As line_fft_ct_from, but stage s writes its outputs to bufs[(PAR + s) & 1]
-// and needs a single barrier per exchange: a buffer is written again only two
+// (each buffer with its own index map) and needs a single barrier per exchange: a buffer is written again only two
 // exchanges later, after every thread has passed the barrier that follows its
 // last read of it.  The caller must not read either buffer concurrently with
 // the first exchange's writes to bufs[PAR].
-template <bool INV, int L, int S, int PAR, int E, typename C, typename Map>
+template <bool INV, int L, int S, int PAR, int E, typename C, typename Map0, typename Map1>
 __device__ __forceinline__ void line_fft_ct_db(C (&v)[E], int t, const C *__restrict__ tw, C *buf0, C *buf1,
-                                               const Map &map)
+                                               const Map0 &map0, const Map1 &map1)
 {
     constexpr int NST = ct_nst(L, E);
     if constexpr (S < NST) {
@@ -415,13 +469,17 @@ __device__ __forceinline__ void line_fft_ct_db(C (&v)[E], int t, const C *__rest
         constexpr int NS = ct_ns(L, S, E);
         constexpr int TL = L / E;
         constexpr bool LAST = (S + 1 == NST);
-        C *sm = ((PAR + S) & 1) ? buf1 : buf0;
-        fft_stage_ct<R, INV, LAST, TL, NS, L / (NS * R)>(v, t, tw, sm, map, true);
+        constexpr bool ONE = ((PAR + S) & 1) != 0;
+        if constexpr (ONE) {
+            fft_stage_ct<R, INV, LAST, TL, NS, L / (NS * R)>(v, t, tw, buf1, map1, true);
+        } else {
+            fft_stage_ct<R, INV, LAST, TL, NS, L / (NS * R)>(v, t, tw, buf0, map0, true);
+        }
         if constexpr (!LAST) {
             __syncthreads();
 #pragma unroll
-            for (int m = 0; m < E; ++m) v[m] = sm[map(t + m * TL)];
-            line_fft_ct_db<INV, L, S + 1, PAR>(v, t, tw, buf0, buf1, map);
+            for (int m = 0; m < E; ++m) v[m] = ONE ? buf1[map1(t + m * TL)] : buf0[map0(t + m * TL)];
+            line_fft_ct_db<INV, L, S + 1, PAR>(v, t, tw, buf0, buf1, map0, map1);
         }
     }
 }
@@ -435,7 +493,7 @@ __device__ __forceinline__ void line_fft_any(C (&v)[E], int t, const LinePlan &p
                                              C *sm, const Map &map, bool active)
 {
     if constexpr (LC > 0) {
-        static_assert(ct_E(LC) == E, "compile-time plan needs its own points per thread");
+        static_assert(ct_E(LC) == E || E == 32, "compile-time plan needs its own points per thread");
         line_fft_ct_from<INV, LC, 0>(v, t, tw, sm, map, active);
     } else {
         line_fft<INV>(v, t, pl, tw, sm, map, active);

@@ -43,7 +43,8 @@ struct TmaArgs {
 bool tma_supported(int L);
 // cfg 0: 64 KiB tiles, 16 points per thread, one 512-thread block per SM;
 // cfg 1: 32 KiB tiles, 16 points per thread, 256-thread blocks, two per SM;
-// cfg 2: 32 KiB tiles, 8 points per thread, 512-thread blocks, two per SM.
+// cfg 2: 32 KiB tiles, 8 points per thread, 512-thread blocks, two per SM;
+// cfg 3: 32 KiB tiles, 32 points per thread (radix-32), 128-thread blocks.
 int tma_columns(int L, int cfg);
 int tma_threads(int L, int cfg);
 size_t tma_smem_bytes(int L, int cfg);

@@ -27,9 +27,11 @@ constexpr uint64_t kWaitLimitNs = 2000000000ull; // 2 s per copy, then PSOLVE_ER
 // CFG 2: as NARROW but 8 points per thread (twice the threads, about half
 // the registers each), so 32 warps per SM hide the barrier and shared-memory
 // latencies of the butterflies.
+// CFG 3: as NARROW but 32 points per thread (radix-32 register butterflies:
+// one exchange per transform of 512 points instead of two).
 template <int L, int CFG> struct TmaShape {
     static constexpr int NARROW = CFG > 0 ? 1 : 0;
-    static constexpr int E = CFG == 2 ? 8 : 16;
+    static constexpr int E = CFG == 2 ? 8 : (CFG == 3 ? 32 : 16);
     static constexpr int TL = L / E;
     static constexpr int W = (8192 / L) >> NARROW;  // columns per tile
     static constexpr int NT = W * TL;               // threads per block
@@ -53,8 +55,8 @@ __global__ void __launch_bounds__(TmaShape<L, CFG>::NT, TmaShape<L, CFG>::MINB)
     extern __shared__ __align__(128) unsigned char smraw[];
     float2 *buf0 = reinterpret_cast<float2 *>(smraw);
     float2 *buf1 = buf0 + L * W;
-    float2 *xbuf = buf1 + L * W; // exchange buffer alternating with the tile's own
-    float2 *stw = xbuf + L * W;
+    float2 *xbuf = buf1 + L * W; // exchange buffer alternating with the tile's own (padded)
+    float2 *stw = xbuf + (L + L / 16) * W;
     uint64_t *bar = reinterpret_cast<uint64_t *>(stw + L);
     int *abort_flag = reinterpret_cast<int *>(bar + 2);
     // tensor-core state after the FP32 layout: MMA barrier, counters, DFT matrices
@@ -123,6 +125,7 @@ __global__ void __launch_bounds__(TmaShape<L, CFG>::NT, TmaShape<L, CFG>::MINB)
     if (tid == 0 && tile < ntiles) issue(tile, buf0, &bar[0]);
 
     const MapStrided map{W, w};
+    const MapStridedPad xmap{W, w};
     for (int k = 0; tile < ntiles; ++k, tile += gridDim.x) {
         float2 *cur = (k & 1) ? buf1 : buf0;
         const long long next = tile + gridDim.x;
@@ -157,7 +160,7 @@ __global__ void __launch_bounds__(TmaShape<L, CFG>::NT, TmaShape<L, CFG>::MINB)
         } else {
             // Exchanges alternate xbuf, cur, xbuf, ...: the first writes go to
             // xbuf, so the tile reads above need no barrier of their own.
-            line_fft_ct_db<KIND == 1, L, 0, 0>(v, t, stw, xbuf, cur, map);
+            line_fft_ct_db<KIND == 1, L, 0, 0>(v, t, stw, xbuf, cur, xmap, map);
         }
 
         float2 *base;
@@ -181,7 +184,7 @@ __global__ void __launch_bounds__(TmaShape<L, CFG>::NT, TmaShape<L, CFG>::MINB)
             } else {
                 // Continue the alternation where the forward transform left it.
                 constexpr int PAR = ct_exchanges(L, E) & 1;
-                line_fft_ct_db<true, L, 0, PAR>(v, t, stw, xbuf, cur, map);
+                line_fft_ct_db<true, L, 0, PAR>(v, t, stw, xbuf, cur, xmap, map);
             }
             step = (long long)TL * a.ny * a.M;
             base = a.data + inst * a.sInst + (long long)y * a.M + col + (long long)t * a.ny * a.M;
@@ -200,8 +203,9 @@ __global__ void __launch_bounds__(TmaShape<L, CFG>::NT, TmaShape<L, CFG>::MINB)
         // Packed column pairs, one group of W/2 pairs per block-iteration.
         const long long npt = (a.npairs + W / 2 - 1) / (W / 2);
         for (long long p = blockIdx.x; p < npt; p += gridDim.x) {
-            xpair_block<float, E, (E == 16 ? L : 0)>(reinterpret_cast<float *>(a.data), L, a.ny, a.M, a.sInst,
-                                                     a.npairs, a.coef, a.pl_x, W, TL, p, t, w, stw, buf0);
+            xpair_block<float, E, (E == 16 || E == 32 ? L : 0)>(reinterpret_cast<float *>(a.data), L, a.ny, a.M,
+                                                                 a.sInst, a.npairs, a.coef, a.pl_x, W, TL, p, t,
+                                                                 w, stw, buf0);
             __syncthreads();
         }
     }
@@ -229,11 +233,15 @@ cudaError_t run(const CUtensorMap &map, const TmaArgs &a, unsigned grid, cudaStr
 
 } // namespace
 
-size_t tma_smem_bytes(int L, int narrow) { return (size_t)3 * (8192 >> (narrow > 0 ? 1 : 0)) * 8 + (size_t)L * 8 + 2 * 8 + 16; }
+size_t tma_smem_bytes(int L, int narrow)
+{
+    const size_t tile = (size_t)(8192 >> (narrow > 0 ? 1 : 0)) * 8;
+    return 3 * tile + tile / 16 + (size_t)L * 8 + 2 * 8 + 16;
+}
 
 int tma_columns(int L, int cfg) { return (8192 / L) >> (cfg > 0 ? 1 : 0); }
 
-int tma_threads(int L, int cfg) { return tma_columns(L, cfg) * L / (cfg == 2 ? 8 : 16); }
+int tma_threads(int L, int cfg) { return tma_columns(L, cfg) * L / (cfg == 2 ? 8 : (cfg == 3 ? 32 : 16)); }
 
 bool tma_supported(int L) { return L == 256 || L == 512 || L == 1024; }
 
@@ -265,6 +273,7 @@ cudaError_t launch_strided_tma(const CUtensorMap &map, const TmaArgs &a, int L, 
     return run<LL, 2, CF, false>(map, a, grid, s);
 #define PSOLVE_TMA_CASE(LL)                                                             \
     case LL:                                                                            \
+        if (cfg == 3) { PSOLVE_TMA_KIND(LL, 3) }                                        \
         if (cfg == 2) { PSOLVE_TMA_KIND(LL, 2) }                                        \
         if (cfg == 1) { PSOLVE_TMA_KIND(LL, 1) }                                        \
         PSOLVE_TMA_KIND(LL, 0)
