@@ -87,11 +87,24 @@ psolve_status psolve_execute(psolve_plan *plan, const void *f, void *u, void *st
  * the same operator; it is the backward of psolve_execute. */
 psolve_status psolve_adjoint(psolve_plan *plan, const void *g, void *grad_f, void *stream);
 
-/* psolve_execute on HOST buffers: copies f_host to the device, solves, copies
- * u back, all on `stream`, and synchronises the stream before returning.
- * Uses a device buffer owned by the plan (allocated on first use). */
+/* psolve_execute on HOST buffers, synchronous on `stream`.  Uses a device
+ * buffer owned by the plan (allocated on first use) for the spectrum.  When
+ * both buffers are pinned (page-locked, e.g. cudaHostAlloc) and the plan is
+ * of equal grids, the first pass reads f and the last pass writes u directly
+ * across the host link; otherwise f is copied in and u copied out.  Either
+ * way f_host and u_host may not overlap. */
 psolve_status psolve_execute_host(psolve_plan *plan, const void *f_host, void *u_host,
                                   void *stream);
+
+/* Asynchronous psolve_execute_host for pipelines: enqueue on `stream` and
+ * return at once.  f is copied in and u copied out by the copy engines
+ * (pinned buffers make these asynchronous).  The plan keeps two device
+ * staging buffers and uses them in turn, each guarded by an event, so
+ * consecutive calls issued on different streams overlap one solve's output
+ * copy with the next one's input copy and kernels.  f_host and u_host must stay valid and unchanged
+ * until the work on `stream` completes; synchronise the streams to collect
+ * u.  Calls for one plan must come from one host thread. */
+psolve_status psolve_execute_host_async(psolve_plan *plan, const void *f_host, void *u_host, void *stream);
 
 /* Free everything the plan owns.  The plan pointer is invalid afterwards. */
 psolve_status psolve_destroy(psolve_plan *plan);

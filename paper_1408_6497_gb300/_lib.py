@@ -22,7 +22,7 @@ STATUS = {0: "PSOLVE_OK", 1: "PSOLVE_ERR_INVALID_ARG", 2: "PSOLVE_ERR_UNSUPPORTE
 
 # Every symbol include/psolve.h declares.
 EXPORTS = ("psolve_plan_create", "psolve_plan_create_many", "psolve_execute", "psolve_adjoint",
-           "psolve_execute_host", "psolve_destroy", "psolve_instance_offset",
+           "psolve_execute_host", "psolve_execute_host_async", "psolve_destroy", "psolve_instance_offset",
            "psolve_total_elements", "psolve_get_status", "psolve_debug_kvec",
            "psolve_error_norms", "psolve_autotune", "psolve_set_profiling", "psolve_pass_times", "psolve_pass_name",
            "psolve_launches_per_solve", "psolve_debug_set_wait", "psolve_debug_tc_dft16",
@@ -56,7 +56,7 @@ def load(path: str | None = None):
         ip = ctypes.POINTER(ctypes.c_int)
         lib.psolve_plan_create.argtypes = [i, i, i, i, i, pp]
         lib.psolve_plan_create_many.argtypes = [ip, ip, ip, i, i, pp]
-        for name in ("psolve_execute", "psolve_adjoint", "psolve_execute_host"):
+        for name in ("psolve_execute", "psolve_adjoint", "psolve_execute_host", "psolve_execute_host_async"):
             getattr(lib, name).argtypes = [vp, vp, vp, vp]
         lib.psolve_destroy.argtypes = [vp]
         lib.psolve_instance_offset.argtypes = [vp, i]

@@ -125,6 +125,18 @@ class Plan:
         _lib.check(rc, "psolve_execute_host")
         return u_host
 
+    def execute_host_async(self, f_host: torch.Tensor, u_host: torch.Tensor, stream=None) -> torch.Tensor:
+        """Enqueue a host-buffer solve without waiting (pinned tensors go
+        straight across the host link); alternate streams to overlap
+        consecutive solves, then synchronise them."""
+        if f_host.numel() != self.total or u_host.numel() != self.total:
+            raise ValueError(f"host tensors must hold {self.total} elements")
+        with torch.cuda.device(self.device):
+            rc = self.lib.psolve_execute_host_async(self.handle, f_host.data_ptr(), u_host.data_ptr(),
+                                                    _stream_handle(stream, self.device))
+        _lib.check(rc, "psolve_execute_host_async")
+        return u_host
+
     def status(self, stream=None) -> None:
         rc = self.lib.psolve_get_status(self.handle, _stream_handle(stream, self.device))
         _lib.check(rc, "psolve_get_status")

@@ -201,6 +201,36 @@ def test_execute_host_matches_device():
     np.testing.assert_array_equal(u_dev, u_host)
 
 
+@pytest.mark.parametrize("prec,shape", [("f32", (32, 16, 48)), ("f32", (128, 256, 512)), ("f64", (24, 24, 32))])
+def test_execute_host_pinned_zero_copy(prec, shape, monkeypatch):
+    """Pinned buffers take the path where the first pass reads f and the last
+    writes u across the host link; it must equal the device solve."""
+    f = torch.from_numpy(wl.random_field(shape, seed=13).astype(NP[prec]).ravel()).pin_memory()
+    u = torch.empty_like(f).pin_memory()
+    plan = Plan(shape, dtype=prec)
+    u_dev = plan.execute(f.cuda()).cpu()
+    plan.execute_host(f, u)
+    assert torch.equal(u, u_dev)
+    monkeypatch.setenv("PSOLVE_ZERO_COPY", "0")
+    u2 = torch.empty_like(f).pin_memory()
+    plan.execute_host(f, u2)
+    assert torch.equal(u2, u_dev)
+
+
+def test_execute_host_async_pipelined():
+    shape = (64, 128, 256)
+    plan = Plan(shape, dtype="f32")
+    fs = [torch.from_numpy(wl.random_field(shape, seed=60 + k).astype(np.float32).ravel()).pin_memory()
+          for k in range(4)]
+    us = [torch.empty_like(f).pin_memory() for f in fs]
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    for k in range(4):
+        plan.execute_host_async(fs[k], us[k], streams[k % 2])
+    torch.cuda.synchronize()
+    for k in range(4):
+        assert torch.equal(us[k], plan.execute(fs[k].cuda()).cpu())
+
+
 def test_adjoint_symmetry_and_autograd_fp64():
     shape = (16, 12, 8)
     x = torch.from_numpy(wl.random_field(shape, seed=1)).cuda()
