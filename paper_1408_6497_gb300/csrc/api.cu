@@ -51,6 +51,7 @@ struct Group {
     int Wz, Wy, Wx;
     int cfg_y, cfg_x;    // TMA configuration of the y / x pass (-1: per-tile kernel)
     int fused;           // z and y passes fused per plane through L2: cluster size, 0 = off
+    int zbulk;           // z passes by the persistent bulk-copy kernel (1) or per-tile blocks (0)
 };
 
 bool factor23(int n, int &a, int &b)
@@ -422,6 +423,7 @@ void apply_tuning_cache(psolve_plan *p)
             const int keep = g.Wz;
             g.Wz = it->second.W;
             if (g.Wz * g.pz.TL > max_threads(fp64, g.pz.E) || z_smem(g, p->dtype) > kSmemCap) g.Wz = keep;
+            if (it->second.cfg < 0) g.zbulk = 0; // the tuner found the per-tile kernels faster
         }
         it = m.find(tune_key(p, path, 'f', g.ny, g.M));
         if (it != m.end() && p->dtype == PSOLVE_F32 && fused_supported(g.M, g.ny) && g.pz.E == 16 &&
@@ -430,7 +432,7 @@ void apply_tuning_cache(psolve_plan *p)
         it = m.find(tune_key(p, path, 'y', g.ny, g.M));
         if (it != m.end()) {
             const TuneChoice c = it->second;
-            if (c.cfg >= 0 && tma_fits(p, g.ny, g.M, c.cfg) && !(p->dtype == PSOLVE_F32_TC && c.cfg > 1)) g.cfg_y = c.cfg;
+            if (c.cfg >= 0 && c.cfg <= 4 && tma_fits(p, g.ny, g.M, c.cfg) && !(p->dtype == PSOLVE_F32_TC && c.cfg > 1)) g.cfg_y = c.cfg;
             else if (c.cfg < 0 && !(p->dtype == PSOLVE_F32_TC && g.cfg_y >= 0) && c.W >= 1 && c.W <= g.M && c.W * g.py.TL <= max_threads(fp64, g.py.E) &&
                      s_smem(g.ny, c.W, p->dtype) <= kSmemCap) {
                 g.cfg_y = -1;
@@ -440,7 +442,7 @@ void apply_tuning_cache(psolve_plan *p)
         it = m.find(tune_key(p, path, 'x', g.nx, g.M));
         if (it != m.end()) {
             const TuneChoice c = it->second;
-            if (c.cfg >= 0 && tma_fits(p, g.nx, g.M, c.cfg) && !(p->dtype == PSOLVE_F32_TC && c.cfg > 1)) g.cfg_x = c.cfg;
+            if (c.cfg >= 0 && c.cfg <= 4 && tma_fits(p, g.nx, g.M, c.cfg) && !(p->dtype == PSOLVE_F32_TC && c.cfg > 1)) g.cfg_x = c.cfg;
             else if (c.cfg < 0 && !(p->dtype == PSOLVE_F32_TC && g.cfg_x >= 0) && c.W >= 2 && c.W * g.px.TL <= max_threads(fp64, g.px.E) &&
                      s_smem(g.nx, c.W, p->dtype) <= kSmemCap) {
                 g.cfg_x = -1;
@@ -650,11 +652,19 @@ psolve_status build_plan(const std::vector<int> &nx, const std::vector<int> &ny,
         const char *nv = std::getenv("PSOLVE_TMA_NARROW");
         int ny_ = 0, nx_ = 0;
         if (nv && std::sscanf(nv, "%d,%d", &ny_, &nx_) == 2) {
-            p->tma_narrow_y = ny_ < 0 || ny_ > 3 ? 0 : ny_;
-            p->tma_narrow_x = nx_ < 0 || nx_ > 3 ? 0 : nx_;
+            p->tma_narrow_y = ny_ < 0 || ny_ > 4 ? 0 : ny_;
+            p->tma_narrow_x = nx_ < 0 || nx_ > 4 ? 0 : nx_;
         }
     }
     for (auto &g : p->groups) {
+        {
+            const char *zb = std::getenv("PSOLVE_ZBULK");
+            const long long rows = (long long)g.count * g.nx * g.ny;
+            g.zbulk = (dtype != PSOLVE_F64 && z_bulk_supported(g.M) && g.pz.E == 16 &&
+                       rows % z_bulk_rows(g.M) == 0 && !(zb && zb[0] == '0'))
+                          ? 1
+                          : 0;
+        }
         g.fused = 0;
         if (uniform && dtype == PSOLVE_F32 && fused_supported(g.M, g.ny) && g.pz.E == 16 && g.py.E == 16) {
             // Off by default (measured slower than the separate TMA passes on
@@ -781,7 +791,8 @@ psolve_status run_tma_pass(const psolve_plan *p, const Group &g, T *ui, int kind
             return fail(PSOLVE_ERR_INTERNAL, "no 8-point plan for the x line");
         long long work = a.main_tiles;
         if (kind == 2) work = std::max(work, (a.npairs + W / 2 - 1) / (W / 2));
-        const unsigned grid = (unsigned)std::min<long long>(work, (long long)p->num_sms * (narrow ? 2 : 1));
+        const int per_sm = (narrow >= 1 && narrow <= 3) ? 2 : 1;
+        const unsigned grid = (unsigned)std::min<long long>(work, (long long)p->num_sms * per_sm);
         cudaError_t e = launch_strided_tma(map, a, L, kind, narrow, grid, s);
         if (e != cudaSuccess) return cuda_fail(e, "TMA pass");
         return PSOLVE_OK;
@@ -792,12 +803,31 @@ psolve_status run_tma_pass(const psolve_plan *p, const Group &g, T *ui, int kind
 // of a group with its current tile choices.
 template <typename T>
 psolve_status launch_pass(const psolve_plan *p, const Group &g, int kind, const T *fi, T *ui, cudaStream_t s,
-                          bool force_runtime = false, T *zout = nullptr)
+                          bool force_runtime = false, T *zout = nullptr, bool host_io = false)
 {
     using C = typename cplx_of<T>::type;
     const C *tab = reinterpret_cast<const C *>(p->tables);
     const int dtype = p->dtype;
     cudaError_t e;
+    if constexpr (sizeof(T) == 4) {
+        // Bulk-copy z passes read/write device memory only (host_io: f or u
+        // is pinned host memory, handled by the per-tile kernels' loads).
+        if ((kind == 0 || kind == 4) && g.zbulk && !force_runtime && !host_io) {
+            ZBulkArgs zb{};
+            zb.real_in = fi;
+            zb.real_out = (kind == 4 && zout) ? zout : ui;
+            zb.spec = reinterpret_cast<float2 *>(ui);
+            zb.rows = (long long)g.count * g.nx * g.ny;
+            zb.tw = tab + g.tw_z;
+            zb.post = tab + g.post;
+            zb.status = p->status;
+            const long long ntiles = zb.rows / z_bulk_rows(g.M);
+            const unsigned grid = (unsigned)std::min<long long>(ntiles, 2LL * p->num_sms);
+            e = launch_z_bulk(zb, g.M, kind == 4, grid, s);
+            if (e != cudaSuccess) return cuda_fail(e, kind == 0 ? "z forward pass" : "z inverse pass");
+            return PSOLVE_OK;
+        }
+    }
     if (kind == 0 || kind == 4) {
         ZArgs<T> z{};
         z.in = kind == 0 ? fi : ui;
@@ -906,7 +936,7 @@ psolve_status launch_fused(const psolve_plan *p, const Group &g, bool inverse, c
 // `uout`, if given, receives u from the last pass (the spectrum stays in u).
 template <typename T>
 psolve_status run_group(const psolve_plan *p, const Group &g, const T *f, T *u, cudaStream_t s,
-                        const std::vector<cudaEvent_t> *ev, T *uout = nullptr)
+                        const std::vector<cudaEvent_t> *ev, T *uout = nullptr, bool host_io = false)
 {
     const T *fi = f + g.off0;
     T *ui = u + g.off0;
@@ -929,7 +959,7 @@ psolve_status run_group(const psolve_plan *p, const Group &g, const T *f, T *u, 
         return PSOLVE_OK;
     }
     for (int kind = 0; kind < kPasses; ++kind) {
-        psolve_status st = launch_pass<T>(p, g, kind, fi, ui, s, false, kind == 4 ? uo : nullptr);
+        psolve_status st = launch_pass<T>(p, g, kind, fi, ui, s, false, kind == 4 ? uo : nullptr, host_io);
         if (st != PSOLVE_OK) return st;
         if (ev) cudaEventRecord((*ev)[kind + 1], s);
     }
@@ -1131,9 +1161,11 @@ template <typename T> psolve_status autotune_impl(psolve_plan *p, cudaStream_t s
         gt.count = 1;
         gt.off0 = 0;
         if (!p->batched && p->uniform) {
-            // z rows per block
+            // z rows per block of the per-tile kernels, then the bulk-copy kernel
             float best = inf;
             int bw = g.Wz;
+            const int zb0 = g.zbulk;
+            gt.zbulk = 0;
             for (int W : wlist) {
                 gt.Wz = W;
                 if (W * gt.pz.TL > max_threads(fp64, gt.pz.E) || z_smem(gt, p->dtype) > kSmemCap) continue;
@@ -1141,7 +1173,14 @@ template <typename T> psolve_status autotune_impl(psolve_plan *p, cudaStream_t s
                 if (t < best) { best = t; bw = W; }
             }
             g.Wz = gt.Wz = bw;
-            cache[tune_key(p, "pass", 'z', g.M, g.M)] = TuneChoice{bw, -1, 0};
+            int zbest = 0;
+            if (zb0) {
+                gt.zbulk = 1;
+                const float t = timed(gt, 0, false) + timed(gt, 4, false);
+                if (t < best) zbest = 1;
+            }
+            g.zbulk = gt.zbulk = zbest;
+            cache[tune_key(p, "pass", 'z', g.M, g.M)] = TuneChoice{bw, zbest ? 1 : -1, 0};
             // y and x: TMA configurations and per-tile widths
             for (int axis = 0; axis < 2; ++axis) {
                 const int L = axis == 0 ? g.ny : g.nx;
@@ -1152,7 +1191,7 @@ template <typename T> psolve_status autotune_impl(psolve_plan *p, cudaStream_t s
                 // A tensor-core plan keeps its passes on the tensor cores: only
                 // the TMA configurations with tensor-core variants (0, 1) compete.
                 const bool tc = p->dtype == PSOLVE_F32_TC;
-                for (int cfg = 0; cfg < (tc ? 2 : 4) && !fp64; ++cfg) {
+                for (int cfg = 0; cfg < (tc ? 2 : 5) && !fp64; ++cfg) {
                     if (!tma_fits(p, L, g.M, cfg)) continue;
                     if (axis == 0) gt.cfg_y = cfg; else gt.cfg_x = cfg;
                     const float t = timed(gt, kind, false);
@@ -1232,9 +1271,9 @@ psolve_status host_solve(psolve_plan *plan, const void *f_host, void *u_host, vo
         for (const auto &g : plan->groups) {
             psolve_status st = plan->dtype == PSOLVE_F64
                                    ? run_group<double>(plan, g, (const double *)fdev, (double *)stage, s,
-                                                       take_events(plan), (double *)udev)
+                                                       take_events(plan), (double *)udev, true)
                                    : run_group<float>(plan, g, (const float *)fdev, (float *)stage, s,
-                                                      take_events(plan), (float *)udev);
+                                                      take_events(plan), (float *)udev, true);
             if (st != PSOLVE_OK) return st;
         }
         return PSOLVE_OK;

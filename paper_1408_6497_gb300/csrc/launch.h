@@ -44,13 +44,29 @@ bool tma_supported(int L);
 // cfg 0: 64 KiB tiles, 16 points per thread, one 512-thread block per SM;
 // cfg 1: 32 KiB tiles, 16 points per thread, 256-thread blocks, two per SM;
 // cfg 2: 32 KiB tiles, 8 points per thread, 512-thread blocks, two per SM;
-// cfg 3: 32 KiB tiles, 32 points per thread (radix-32), 128-thread blocks.
+// cfg 3: 32 KiB tiles, 32 points per thread (radix-32), 128-thread blocks;
+// cfg 4: 64 KiB tiles, 32 points per thread, one block per SM.
 int tma_columns(int L, int cfg);
 int tma_threads(int L, int cfg);
 size_t tma_smem_bytes(int L, int cfg);
 // kind: 0 = y forward, 1 = y inverse, 2 = x with the spectral division.
 cudaError_t launch_strided_tma(const CUtensorMap &map, const TmaArgs &a, int L, int kind, int cfg,
                                unsigned grid, cudaStream_t s);
+
+// Persistent z passes fed by 1D bulk copies (FP32, M = 256 or 512).
+struct ZBulkArgs {
+    const float *real_in; // forward: f rows
+    float *real_out;      // inverse: u rows
+    float2 *spec;         // packed spectrum rows (forward output, inverse input)
+    long long rows;       // multiple of z_bulk_rows(M)
+    const float2 *tw;     // e^{-2πi j/M}
+    const float2 *post;   // e^{-2πi k/nz}, k < M
+    int *status;
+};
+bool z_bulk_supported(int M);
+int z_bulk_rows(int M);
+size_t z_bulk_smem(int M);
+cudaError_t launch_z_bulk(const ZBulkArgs &a, int M, bool inverse, unsigned grid, cudaStream_t s);
 
 // z and y passes of a plane fused through L2 in one cluster launch.
 constexpr int kFusedThreads = 256;

@@ -29,9 +29,11 @@ constexpr uint64_t kWaitLimitNs = 2000000000ull; // 2 s per copy, then PSOLVE_ER
 // latencies of the butterflies.
 // CFG 3: as NARROW but 32 points per thread (radix-32 register butterflies:
 // one exchange per transform of 512 points instead of two).
+// CFG 4: 64 KiB tiles with 32 points per thread (wide radix-32; for lines of
+// 1024 points, whose narrow tiles would have 32-byte rows).
 template <int L, int CFG> struct TmaShape {
-    static constexpr int NARROW = CFG > 0 ? 1 : 0;
-    static constexpr int E = CFG == 2 ? 8 : (CFG == 3 ? 32 : 16);
+    static constexpr int NARROW = (CFG > 0 && CFG < 4) ? 1 : 0;
+    static constexpr int E = CFG == 2 ? 8 : (CFG >= 3 ? 32 : 16);
     static constexpr int TL = L / E;
     static constexpr int W = (8192 / L) >> NARROW;  // columns per tile
     static constexpr int NT = W * TL;               // threads per block
@@ -239,9 +241,9 @@ size_t tma_smem_bytes(int L, int narrow)
     return 3 * tile + tile / 16 + (size_t)L * 8 + 2 * 8 + 16;
 }
 
-int tma_columns(int L, int cfg) { return (8192 / L) >> (cfg > 0 ? 1 : 0); }
+int tma_columns(int L, int cfg) { return (8192 / L) >> ((cfg > 0 && cfg < 4) ? 1 : 0); }
 
-int tma_threads(int L, int cfg) { return tma_columns(L, cfg) * L / (cfg == 2 ? 8 : (cfg == 3 ? 32 : 16)); }
+int tma_threads(int L, int cfg) { return tma_columns(L, cfg) * L / (cfg == 2 ? 8 : (cfg >= 3 ? 32 : 16)); }
 
 bool tma_supported(int L) { return L == 256 || L == 512 || L == 1024; }
 
@@ -273,6 +275,7 @@ cudaError_t launch_strided_tma(const CUtensorMap &map, const TmaArgs &a, int L, 
     return run<LL, 2, CF, false>(map, a, grid, s);
 #define PSOLVE_TMA_CASE(LL)                                                             \
     case LL:                                                                            \
+        if (cfg == 4) { PSOLVE_TMA_KIND(LL, 4) }                                        \
         if (cfg == 3) { PSOLVE_TMA_KIND(LL, 3) }                                        \
         if (cfg == 2) { PSOLVE_TMA_KIND(LL, 2) }                                        \
         if (cfg == 1) { PSOLVE_TMA_KIND(LL, 1) }                                        \

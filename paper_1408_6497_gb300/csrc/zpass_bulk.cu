@@ -1,0 +1,164 @@
+// Persistent z passes fed by 1D bulk copies, FP32 rows of M = 256 or 512
+// complex points (nz = 512 or 1024).
+//
+// A tile is W consecutive rows (W·nz reals, contiguous in HBM), 32 KiB; one
+// cp.async.bulk brings tile i+1 into shared memory while tile i is being
+// transformed (two buffers, two mbarriers, time-bounded waits).  Threads read
+// their strided class of a row from the tile (conflict-free: a row is
+// contiguous), exchange through a padded buffer (a spare slot every 16
+// points), and store the result row straight from registers.
+//   forward: real row -> M-point FFT -> split post-twiddle -> packed row
+//   inverse: packed row -> pre-twiddle merge -> inverse FFT -> real row
+#include "psolve.h"
+#include "launch.h"
+#include "tma.cuh"
+
+namespace psolve {
+
+namespace {
+
+constexpr uint64_t kZWaitNs = 2000000000ull;
+
+template <int M> struct ZShape {
+    static constexpr int E = 16;
+    static constexpr int TL = M / E;
+    static constexpr int NT = 256;
+    static constexpr int W = NT / TL;                       // rows per tile
+    static constexpr int LP = M + (M >> 4) + 1;             // padded row pitch (complex)
+    static constexpr uint32_t TILE_BYTES = (uint32_t)(W * M * 8);
+};
+
+template <int M, bool INV>
+__global__ void __launch_bounds__(256, 2) k_z_bulk(ZBulkArgs a)
+{
+    using S = ZShape<M>;
+    constexpr int E = S::E, TL = S::TL, W = S::W;
+    extern __shared__ __align__(128) unsigned char smraw[];
+    float2 *buf0 = reinterpret_cast<float2 *>(smraw);
+    float2 *buf1 = buf0 + W * M;
+    float2 *xb = buf1 + W * M;                 // W padded rows
+    float2 *stw = xb + W * S::LP;              // e^{-2πij/M}
+    float2 *spost = stw + M;                   // e^{-2πik/nz}, k < M
+    uint64_t *bar = reinterpret_cast<uint64_t *>(spost + M);
+    int *abort_flag = reinterpret_cast<int *>(bar + 2);
+
+    const int tid = threadIdx.x;
+    const int w = tid / TL, t = tid - w * TL;
+    const long long ntiles = a.rows / W;
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        *abort_flag = 0;
+        fence_mbar_init();
+    }
+    for (int i = tid; i < M; i += blockDim.x) {
+        stw[i] = a.tw[i];
+        spost[i] = a.post[i];
+    }
+    __syncthreads();
+    const float *src = INV ? reinterpret_cast<const float *>(a.spec) : a.real_in;
+    auto issue = [&](long long tile, float2 *dst, uint64_t *b) {
+        mbar_expect_tx(b, S::TILE_BYTES);
+        bulk_load(dst, src + tile * (long long)W * (2 * M), S::TILE_BYTES, b);
+    };
+    long long tile = blockIdx.x;
+    if (tid == 0 && tile < ntiles) issue(tile, buf0, &bar[0]);
+    const MapRow xm{w * S::LP};
+
+    for (int k = 0; tile < ntiles; ++k, tile += gridDim.x) {
+        float2 *cur = (k & 1) ? buf1 : buf0;
+        const long long next = tile + gridDim.x;
+        if (tid == 0) {
+            if (next < ntiles) {
+                fence_proxy_async_smem();
+                issue(next, (k & 1) ? buf0 : buf1, &bar[(k + 1) & 1]);
+            }
+            if (!mbar_wait_bounded(&bar[k & 1], (uint32_t)((k >> 1) & 1), kZWaitNs)) {
+                *abort_flag = 1;
+                atomicExch(a.status, (int)PSOLVE_ERR_TIMEOUT);
+                if (next < ntiles) mbar_wait_bounded(&bar[(k + 1) & 1], (uint32_t)(((k + 1) >> 1) & 1), kZWaitNs);
+            }
+        }
+        __syncthreads();
+        if (*abort_flag) break;
+
+        const long long row = tile * W + w;
+        const float2 *rowp = cur + w * M;
+        float2 v[E];
+        if (!INV) {
+#pragma unroll
+            for (int m = 0; m < E; ++m) v[m] = rowp[t + m * TL];
+            line_fft_ct_from<false, M, 0>(v, t, stw, xb, xm, true);
+            // Z[k] -> X[k] needs Z[M-k]
+#pragma unroll
+            for (int m = 0; m < E; ++m) xb[xm(t + m * TL)] = v[m];
+            __syncthreads();
+            float2 *dst = reinterpret_cast<float2 *>(a.spec) + row * M;
+#pragma unroll
+            for (int m = 0; m < E; ++m) {
+                const int kk = t + m * TL;
+                const float2 z = v[m];
+                if (kk == 0) {
+                    dst[0] = make_float2(z.x + z.y, z.x - z.y);
+                } else {
+                    const float2 zp = xb[xm(M - kk)];
+                    const float2 e = make_float2((z.x + zp.x) * 0.5f, (z.y - zp.y) * 0.5f);
+                    const float2 o = make_float2((z.y + zp.y) * 0.5f, (zp.x - z.x) * 0.5f);
+                    dst[kk] = cadd(e, cmul(o, spost[kk]));
+                }
+            }
+        } else {
+#pragma unroll
+            for (int m = 0; m < E; ++m) {
+                const int kk = t + m * TL;
+                const float2 x = rowp[kk];
+                if (kk == 0) {
+                    v[m] = make_float2(x.x + x.y, x.x - x.y);
+                } else {
+                    const float2 xp = rowp[M - kk];
+                    const float2 e = make_float2(x.x + xp.x, x.y - xp.y);
+                    const float2 o = cmulc(make_float2(x.x - xp.x, x.y + xp.y), spost[kk]);
+                    v[m] = make_float2(e.x - o.y, e.y + o.x);
+                }
+            }
+            line_fft_ct_from<true, M, 0>(v, t, stw, xb, xm, true);
+            float2 *dst = reinterpret_cast<float2 *>(a.real_out + row * (2 * M)) + t;
+#pragma unroll
+            for (int m = 0; m < E; ++m) dst[m * TL] = v[m];
+        }
+        __syncthreads(); // `cur` and `xb` are free for the next tile
+    }
+}
+
+template <int M, bool INV> cudaError_t run(const ZBulkArgs &a, unsigned grid, cudaStream_t s)
+{
+    using S = ZShape<M>;
+    const size_t smem = z_bulk_smem(M);
+    auto kern = k_z_bulk<M, INV>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<grid, S::NT, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+} // namespace
+
+bool z_bulk_supported(int M) { return M == 256 || M == 512; }
+
+int z_bulk_rows(int M) { return 256 / (M / 16); }
+
+size_t z_bulk_smem(int M)
+{
+    const int W = z_bulk_rows(M);
+    const int LP = M + (M >> 4) + 1;
+    return (size_t)(2 * W * M + W * LP + 2 * M) * 8 + 2 * 8 + 16;
+}
+
+cudaError_t launch_z_bulk(const ZBulkArgs &a, int M, bool inverse, unsigned grid, cudaStream_t s)
+{
+    if (M == 256) return inverse ? run<256, true>(a, grid, s) : run<256, false>(a, grid, s);
+    if (M == 512) return inverse ? run<512, true>(a, grid, s) : run<512, false>(a, grid, s);
+    return cudaErrorInvalidValue;
+}
+
+} // namespace psolve
