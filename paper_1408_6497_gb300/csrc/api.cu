@@ -316,6 +316,16 @@ void release(psolve_plan *p)
 // Whether the persistent TMA pass applies to lines of length L over M columns.
 int tma_variant(int setting, int L) { return setting >= 0 ? setting : (tma_columns(L, 1) >= 8 ? 1 : 0); }
 
+// Untuned FP32 choice per axis (measured on GB300): radix-32 tiles for the
+// long lines, 64 KiB ones for y and 1024-point x lines, 32 KiB ones for the
+// 512-point x lines (two blocks per SM hide the double transform's latency).
+int tma_default(int L, bool x_axis)
+{
+    if (L >= 1024) return 4;
+    if (L == 512) return x_axis ? 3 : 4;
+    return 1;
+}
+
 bool tma_fits(const psolve_plan *p, int L, int M, int narrow)
 {
     return p->use_tma && p->dtype != PSOLVE_F64 && tma_supported(L) && (M % 2) == 0 &&
@@ -673,10 +683,18 @@ psolve_status build_plan(const std::vector<int> &nx, const std::vector<int> &ny,
             g.fused = 0;
             if (fe && fe[0] >= '1' && fe[0] <= '8') g.fused = fe[0] - '0';
         }
-        g.cfg_y = tma_fits(p.get(), g.ny, g.M, tma_variant(p->tma_narrow_y, g.ny))
-                      ? tma_variant(p->tma_narrow_y, g.ny) : -1;
-        g.cfg_x = tma_fits(p.get(), g.nx, g.M, tma_variant(p->tma_narrow_x, g.nx))
-                      ? tma_variant(p->tma_narrow_x, g.nx) : -1;
+        auto pick = [&](int setting, int L, bool x_axis) {
+            if (setting >= 0 || dtype == PSOLVE_F32_TC) {
+                const int c = tma_variant(setting, L);
+                return tma_fits(p.get(), L, g.M, c) ? c : -1;
+            }
+            // preferred configuration, else the narrower tiles that fit
+            for (int c : {tma_default(L, x_axis), 3, 1})
+                if (tma_fits(p.get(), L, g.M, c)) return c;
+            return -1;
+        };
+        g.cfg_y = pick(p->tma_narrow_y, g.ny, false);
+        g.cfg_x = pick(p->tma_narrow_x, g.nx, true);
     }
     apply_tuning_cache(p.get());
     e = cudaMalloc(&p->tables, tcount * csize(dtype));

@@ -35,12 +35,26 @@ template <typename C> __device__ __forceinline__ C cmulc(C a, C b)
 }
 template <typename C, typename S> __device__ __forceinline__ C cscale(C a, S s) { return {a.x * s, a.y * s}; }
 
-#if defined(__CUDA_ARCH__) && (__CUDA_ARCH__ >= 1000) && defined(PSOLVE_F32X2)
-// Blackwell packed FP32x2 arithmetic: one instruction per complex add/sub
-// (opt-in: measured slower than scalar FADDs on the z passes).
+#if defined(__CUDA_ARCH__) && (__CUDA_ARCH__ >= 1000) && !defined(PSOLVE_NO_F32X2)
+// Blackwell packed FP32x2 arithmetic: one instruction per complex add, sub
+// (a - b as the fused b·(-1) + a, exact) or real scale.  Products and ±i
+// rotations stay scalar: on pairs they need the swapped pair (a.y, a.x),
+// whose moves cost more than the packing saves (measured).
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
-__device__ __forceinline__ float2 csub(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return __fmul2_rn(a, make_float2(s, s)); }
 #endif
+
+// a · (c + i s) for a real pair (c, s).
+template <typename C, typename T> __device__ __forceinline__ C cmul_cs(C a, T c, T s)
+{
+    return C{a.x * c - a.y * s, a.x * s + a.y * c};
+}
+// a - i·b (DN = true) or a + i·b, the odd outputs of the radix-4 butterfly.
+template <bool DN, typename C> __device__ __forceinline__ C cadd_rot(C a, C b)
+{
+    return DN ? C{a.x + b.y, a.y - b.x} : C{a.x - b.y, a.y + b.x};
+}
 template <typename C> __device__ __forceinline__ C cconj(C a) { return {a.x, -a.y}; }
 
 // Multiply by -i (forward direction) or +i (inverse direction).
@@ -84,7 +98,7 @@ template <bool INV, int M, typename C> __device__ __forceinline__ C mul_w16(C a)
     } else {
         const T c = (T)Oct::c[M];
         const T s = INV ? (T)Oct::s[M] : -(T)Oct::s[M];
-        return C{a.x * c - a.y * s, a.x * s + a.y * c};
+        return cmul_cs(a, c, s);
     }
 }
 
@@ -120,13 +134,8 @@ template <bool INV, typename C> __device__ __forceinline__ void dft4(C *a)
     a[0] = cadd(a0, a2);
     a[2] = csub(a0, a2);
     // a1 ∓ i·d (forward: out1 = a1 - i d, out3 = a1 + i d)
-    if (INV) {
-        a[1] = C{a1.x - d.y, a1.y + d.x};
-        a[3] = C{a1.x + d.y, a1.y - d.x};
-    } else {
-        a[1] = C{a1.x + d.y, a1.y - d.x};
-        a[3] = C{a1.x - d.y, a1.y + d.x};
-    }
+    a[1] = cadd_rot<!INV>(a1, d);
+    a[3] = cadd_rot<INV>(a1, d);
 }
 
 template <bool INV, typename C> __device__ __forceinline__ void dft8(C *a)
@@ -199,7 +208,7 @@ template <bool INV, int K, typename C> __device__ __forceinline__ C mul_w32(C a)
         const T s0 = (T)Hex::c[3 - (k - 1) / 2]; // sin(πk/16) = cos(π(8-k)/16)
         const T c = K < 8 ? c0 : -c0;
         const T s = INV ? s0 : -s0;
-        return C{a.x * c - a.y * s, a.x * s + a.y * c};
+        return cmul_cs(a, c, s);
     }
 }
 
