@@ -265,11 +265,13 @@ struct MapStrided { // [p][w], pitch P: lines side by side (y and x passes)
     int P, w;
     __device__ __forceinline__ int operator()(int p) const { return p * P + w; }
 };
-struct MapStridedPad { // [p][w] with a spare row after every 16 rows: the rows
-                       // 16 apart written together by the first Stockham stage
-                       // then fall in different banks (row step 17·P)
+// [p][w] with a spare row after every 2^SH rows.  The first Stockham stage
+// (radix R = 2^SH) writes rows R apart from neighbouring threads; the spare
+// row makes that distance R + 1, so with rows of 8 columns (half the banks)
+// neighbouring threads land in opposite bank halves instead of the same one.
+template <int SH = 4> struct MapStridedPad {
     int P, w;
-    __device__ __forceinline__ int operator()(int p) const { return (p + (p >> 4)) * P + w; }
+    __device__ __forceinline__ int operator()(int p) const { return (p + (p >> SH)) * P + w; }
 };
 struct MapRow { // [w][p], one padded row per line (z passes)
     int base;

@@ -127,7 +127,9 @@ __global__ void __launch_bounds__(TmaShape<L, CFG>::NT, TmaShape<L, CFG>::MINB)
     if (tid == 0 && tile < ntiles) issue(tile, buf0, &bar[0]);
 
     const MapStrided map{W, w};
-    const MapStridedPad xmap{W, w};
+    // spare row every R0 rows, R0 = the radix of the first stage
+    constexpr int PADSH = ct_radix(L, 0, E) >= 32 ? 5 : 4;
+    const MapStridedPad<PADSH> xmap{W, w};
     for (int k = 0; tile < ntiles; ++k, tile += gridDim.x) {
         float2 *cur = (k & 1) ? buf1 : buf0;
         const long long next = tile + gridDim.x;
