@@ -45,9 +45,12 @@ typedef enum {
     PSOLVE_F32_TC = 2   /* float in/out; radix-16 stages of the y and x passes on the tensor
                            cores (tcgen05, BF16 hi/lo operands, FP32 accumulation in TMEM)
                            where those passes use the TMA kernels (lines of 256, 512 or 1024
-                           points); every other stage in FP32.  psolve_pass_name reports
-                           "yfwd_tc", "xdiv_tc", "yinv_tc" for the passes that do.  Equal-grid
-                           plans only. */
+                           points); every other stage in FP32.  Lines of 512 points use the
+                           plan 32 × 16 by default (radix-32 stage in FP32, the radix-16
+                           stage on the tensor cores); the others, and 512 when asked, plans
+                           of radix-16 stages (16 × 16 × …), each on the tensor cores.
+                           psolve_pass_name reports "yfwd_tc", "xdiv_tc", "yinv_tc" for the
+                           passes that do.  Equal-grid plans only. */
 } psolve_dtype;
 
 typedef enum {

@@ -319,6 +319,10 @@ int tma_variant(int setting, int L) { return setting >= 0 ? setting : (tma_colum
 // Untuned FP32 choice per axis (measured on GB300): radix-32 tiles for the
 // long lines, 64 KiB ones for y and 1024-point x lines, 32 KiB ones for the
 // 512-point x lines (two blocks per SM hide the double transform's latency).
+// TMA configurations with tensor-core variants: 16 points per thread (0, 1)
+// for every line length, 32 points per thread (3, 4) for 512-point lines.
+bool tc_cfg_ok(int cfg, int L) { return cfg == 0 || cfg == 1 || (L == 512 && (cfg == 3 || cfg == 4)); }
+
 int tma_default(int L, bool x_axis)
 {
     if (L >= 1024) return 4;
@@ -442,7 +446,7 @@ void apply_tuning_cache(psolve_plan *p)
         it = m.find(tune_key(p, path, 'y', g.ny, g.M));
         if (it != m.end()) {
             const TuneChoice c = it->second;
-            if (c.cfg >= 0 && c.cfg <= 4 && tma_fits(p, g.ny, g.M, c.cfg) && !(p->dtype == PSOLVE_F32_TC && c.cfg > 1)) g.cfg_y = c.cfg;
+            if (c.cfg >= 0 && c.cfg <= 4 && tma_fits(p, g.ny, g.M, c.cfg) && !(p->dtype == PSOLVE_F32_TC && !tc_cfg_ok(c.cfg, g.ny))) g.cfg_y = c.cfg;
             else if (c.cfg < 0 && !(p->dtype == PSOLVE_F32_TC && g.cfg_y >= 0) && c.W >= 1 && c.W <= g.M && c.W * g.py.TL <= max_threads(fp64, g.py.E) &&
                      s_smem(g.ny, c.W, p->dtype) <= kSmemCap) {
                 g.cfg_y = -1;
@@ -452,7 +456,7 @@ void apply_tuning_cache(psolve_plan *p)
         it = m.find(tune_key(p, path, 'x', g.nx, g.M));
         if (it != m.end()) {
             const TuneChoice c = it->second;
-            if (c.cfg >= 0 && c.cfg <= 4 && tma_fits(p, g.nx, g.M, c.cfg) && !(p->dtype == PSOLVE_F32_TC && c.cfg > 1)) g.cfg_x = c.cfg;
+            if (c.cfg >= 0 && c.cfg <= 4 && tma_fits(p, g.nx, g.M, c.cfg) && !(p->dtype == PSOLVE_F32_TC && !tc_cfg_ok(c.cfg, g.nx))) g.cfg_x = c.cfg;
             else if (c.cfg < 0 && !(p->dtype == PSOLVE_F32_TC && g.cfg_x >= 0) && c.W >= 2 && c.W * g.px.TL <= max_threads(fp64, g.px.E) &&
                      s_smem(g.nx, c.W, p->dtype) <= kSmemCap) {
                 g.cfg_x = -1;
@@ -684,7 +688,15 @@ psolve_status build_plan(const std::vector<int> &nx, const std::vector<int> &ny,
             if (fe && fe[0] >= '1' && fe[0] <= '8') g.fused = fe[0] - '0';
         }
         auto pick = [&](int setting, int L, bool x_axis) {
-            if (setting >= 0 || dtype == PSOLVE_F32_TC) {
+            if (dtype == PSOLVE_F32_TC) {
+                // 32 points per thread and 32 KiB tiles (one tensor-core stage
+                // per 512-point line; measured fastest on both axes) unless a
+                // configuration is asked for
+                int c = tma_variant(setting, L);
+                if (setting < 0 && L == 512 && tma_fits(p.get(), L, g.M, 3)) c = 3;
+                return tma_fits(p.get(), L, g.M, c) && tc_cfg_ok(c, L) ? c : -1;
+            }
+            if (setting >= 0) {
                 const int c = tma_variant(setting, L);
                 return tma_fits(p.get(), L, g.M, c) ? c : -1;
             }
@@ -1207,10 +1219,10 @@ template <typename T> psolve_status autotune_impl(psolve_plan *p, cudaStream_t s
                 float bt = inf;
                 int bcfg = -1, bW = axis == 0 ? g.Wy : g.Wx;
                 // A tensor-core plan keeps its passes on the tensor cores: only
-                // the TMA configurations with tensor-core variants (0, 1) compete.
+                // the TMA configurations with tensor-core variants compete.
                 const bool tc = p->dtype == PSOLVE_F32_TC;
-                for (int cfg = 0; cfg < (tc ? 2 : 5) && !fp64; ++cfg) {
-                    if (!tma_fits(p, L, g.M, cfg)) continue;
+                for (int cfg = 0; cfg < 5 && !fp64; ++cfg) {
+                    if (!tma_fits(p, L, g.M, cfg) || (tc && !tc_cfg_ok(cfg, L))) continue;
                     if (axis == 0) gt.cfg_y = cfg; else gt.cfg_x = cfg;
                     const float t = timed(gt, kind, false);
                     if (t < bt) { bt = t; bcfg = cfg; }

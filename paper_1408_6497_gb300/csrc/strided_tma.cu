@@ -45,15 +45,22 @@ template <int L, int CFG> struct TmaShape {
 
 // KIND: 0 = y forward, 1 = y inverse, 2 = x forward + division + x inverse.
 // TC: radix-16 stages on the tensor cores (BF16 hi/lo, FP32 accumulation in
-// TMEM); the exchange buffer then holds the BF16 operand rows instead (it
-// has exactly their size: one 128-byte row per thread).
+// TMEM).  With 16 points per thread (plans 16·16·…) every radix-16 stage
+// runs there, the exchange buffer holding the BF16 operand rows (it has
+// exactly their size: one 128-byte row per thread).  With 32 points per
+// thread (512 = 32 × 16) the radix-32 stage stays in FP32 and the radix-16
+// stage, the last, runs on the tensor cores per warpgroup (tc32_last_stage),
+// its operand rows in the tile buffer once the tile has been read.
 template <int L, int KIND, int CFG, bool TC>
 __global__ void __launch_bounds__(TmaShape<L, CFG>::NT, TmaShape<L, CFG>::MINB)
     k_strided_tma(const __grid_constant__ CUtensorMap tmap, TmaArgs a)
 {
     using S = TmaShape<L, CFG>;
     constexpr int E = S::E, TL = S::TL, W = S::W;
-    static_assert(!TC || (E == 16 && S::NT % 128 == 0), "tensor-core stages need 16 points per thread");
+    constexpr bool TC32 = TC && E == 32;
+    static_assert(!TC || ((E == 16 || (E == 32 && L == 512)) && S::NT % 128 == 0),
+                  "tensor-core stages: 16 points per thread, or 32 for 512-point lines");
+    constexpr int NWG = S::NT / 128; // warpgroups per block
     extern __shared__ __align__(128) unsigned char smraw[];
     float2 *buf0 = reinterpret_cast<float2 *>(smraw);
     float2 *buf1 = buf0 + L * W;
@@ -61,12 +68,13 @@ __global__ void __launch_bounds__(TmaShape<L, CFG>::NT, TmaShape<L, CFG>::MINB)
     float2 *stw = xbuf + (L + L / 16) * W;
     uint64_t *bar = reinterpret_cast<uint64_t *>(stw + L);
     int *abort_flag = reinterpret_cast<int *>(bar + 2);
-    // tensor-core state after the FP32 layout: MMA barrier, counters, DFT matrices
+    // tensor-core state after the FP32 layout: MMA barrier(s) (one per
+    // warpgroup with 32 points per thread), counters, DFT matrices
     uint64_t *mbar = bar + 4;
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(mbar + 1);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(TC32 ? bar + 6 : mbar + 1);
     uint32_t *tphase = tslot + 1;
     unsigned char *fmat = reinterpret_cast<unsigned char *>(bar + 8);
-    constexpr uint32_t kCols = 32 * (S::NT / 128);
+    constexpr uint32_t kCols = (TC32 ? 64 : 32) * NWG;
 
     const int tid = threadIdx.x;
     const int w = tid % W, t = tid / W;
@@ -77,7 +85,7 @@ __global__ void __launch_bounds__(TmaShape<L, CFG>::NT, TmaShape<L, CFG>::MINB)
         mbar_init(&bar[1], 1);
         *abort_flag = 0;
         if constexpr (TC) {
-            mbar_init(mbar, 1);
+            for (int g = 0; g < (TC32 ? NWG : 1); ++g) mbar_init(mbar + g, 1);
             *tphase = 0;
         }
         fence_mbar_init();
@@ -85,6 +93,8 @@ __global__ void __launch_bounds__(TmaShape<L, CFG>::NT, TmaShape<L, CFG>::MINB)
     }
     for (int i = tid; i < L; i += blockDim.x) stw[i] = a.tw[i];
     TcCtx tc{};
+    Tc32Ctx tc32{};
+    uint32_t nphase = 0; // this warpgroup's completed MMA batches (32 points per thread)
     if constexpr (TC) {
         tc_build_dft16(fmat, fmat + kTcFBytes, fmat + 2 * kTcFBytes, fmat + 3 * kTcFBytes);
         if (tid < 32) tmem_alloc(tslot, kCols);
@@ -104,6 +114,14 @@ __global__ void __launch_bounds__(TmaShape<L, CFG>::NT, TmaShape<L, CFG>::MINB)
         tc.phase = tphase;
         tc.abort = abort_flag;
         tc.status = a.status;
+        tc32.f_hi[0] = tc.f_hi[0];
+        tc32.f_lo[0] = tc.f_lo[0];
+        tc32.f_hi[1] = tc.f_hi[1];
+        tc32.f_lo[1] = tc.f_lo[1];
+        tc32.tmem = tc.tmem;
+        tc32.bar = mbar;
+        tc32.abort = abort_flag;
+        tc32.status = a.status;
     }
 
     // Tile -> TMA coordinates (c0 = first column, c1, c2 of the first row).
@@ -134,7 +152,7 @@ __global__ void __launch_bounds__(TmaShape<L, CFG>::NT, TmaShape<L, CFG>::MINB)
         float2 *cur = (k & 1) ? buf1 : buf0;
         const long long next = tile + gridDim.x;
         if (tid == 0) {
-            if (next < ntiles) {
+            if (next < ntiles && !*abort_flag) {
                 // The other buffer was released by the barrier that ended the
                 // previous iteration; order those generic accesses before TMA.
                 fence_proxy_async_smem();
@@ -157,7 +175,17 @@ __global__ void __launch_bounds__(TmaShape<L, CFG>::NT, TmaShape<L, CFG>::MINB)
         float2 v[E];
 #pragma unroll
         for (int m = 0; m < E; ++m) v[m] = cur[(t + m * TL) * W + w];
-        if constexpr (TC) {
+        if constexpr (TC32) {
+            // radix 32 in FP32, exchange through xbuf, radix 16 on the tensor
+            // cores with operand rows in `cur` (read out above, before the
+            // exchange barrier)
+            tc32.op = reinterpret_cast<unsigned char *>(cur);
+            fft_stage_ct<32, KIND == 1, false, TL, 1, L / 32>(v, t, stw, xbuf, xmap, true);
+            __syncthreads();
+#pragma unroll
+            for (int m = 0; m < E; ++m) v[m] = xbuf[xmap(t + m * TL)];
+            tc32_last_stage<KIND == 1>(v, t, stw, tc32, nphase);
+        } else if constexpr (TC) {
             __syncthreads(); // single-buffer exchanges in `cur`
             line_fft_tc_from<KIND == 1, L, 0>(v, t, stw, cur, map, tc);
             if (*abort_flag) break;
@@ -182,7 +210,16 @@ __global__ void __launch_bounds__(TmaShape<L, CFG>::NT, TmaShape<L, CFG>::MINB)
                 const float d = (k2 == 0) ? 0.f : __fdividef(a.coef, (float)k2);
                 v[m] = cscale(v[m], d);
             }
-            if constexpr (TC) {
+            if constexpr (TC32) {
+                // Every warpgroup is past its forward stages (xbuf reads,
+                // MMAs on `cur`) before xbuf and `cur` are reused.
+                __syncthreads();
+                fft_stage_ct<32, true, false, TL, 1, L / 32>(v, t, stw, xbuf, xmap, true);
+                __syncthreads();
+#pragma unroll
+                for (int m = 0; m < E; ++m) v[m] = xbuf[xmap(t + m * TL)];
+                tc32_last_stage<true>(v, t, stw, tc32, nphase);
+            } else if constexpr (TC) {
                 line_fft_tc_from<true, L, 0>(v, t, stw, cur, map, tc);
                 if (*abort_flag) break;
             } else {
@@ -216,6 +253,12 @@ __global__ void __launch_bounds__(TmaShape<L, CFG>::NT, TmaShape<L, CFG>::MINB)
     if constexpr (TC) {
         tc_fence_before();
         __syncthreads();
+        if constexpr (TC32) {
+            // After a timed-out wait, let issued MMAs drain before TMEM is freed.
+            if (*abort_flag && (tid & 127) == 0)
+                mbar_wait_bounded(mbar + (tid >> 7), (nphase - 1) & 1u, 2000000000ull);
+            __syncthreads();
+        }
         if (tid < 32) {
             tc_fence_after();
             tmem_dealloc(tc.tmem, kCols);
@@ -254,6 +297,17 @@ cudaError_t launch_strided_tma(const CUtensorMap &map, const TmaArgs &a, int L, 
 {
     if (a.tc) {
         if (cfg == 2) return cudaErrorInvalidValue;
+        if (cfg >= 3) { // 32 points per thread: 512-point lines only
+            if (L != 512) return cudaErrorInvalidValue;
+            if (cfg == 3) {
+                if (kind == 0) return run<512, 0, 3, true>(map, a, grid, s);
+                if (kind == 1) return run<512, 1, 3, true>(map, a, grid, s);
+                return run<512, 2, 3, true>(map, a, grid, s);
+            }
+            if (kind == 0) return run<512, 0, 4, true>(map, a, grid, s);
+            if (kind == 1) return run<512, 1, 4, true>(map, a, grid, s);
+            return run<512, 2, 4, true>(map, a, grid, s);
+        }
 #define PSOLVE_TMA_TC(LL)                                                               \
         if (L == LL) {                                                                  \
             if (cfg == 1) {                                                             \

@@ -103,14 +103,16 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&r)[32])
     for (int i = 0; i < 32; ++i) r[i] = __uint_as_float(u[i]);
 }
 
-// Split x into BF16 hi + lo, packed two values per 32-bit word.
+// Split x into BF16 hi + lo, packed two values per 32-bit word (x0 in the
+// low half): one paired conversion for hi, the exact residuals x - hi as a
+// packed difference, one paired conversion for lo.
 __device__ __forceinline__ void bf16_split2(float x0, float x1, uint32_t &hi, uint32_t &lo)
 {
-    const __nv_bfloat16 h0 = __float2bfloat16_rn(x0), h1 = __float2bfloat16_rn(x1);
-    const __nv_bfloat16 l0 = __float2bfloat16_rn(x0 - __bfloat162float(h0));
-    const __nv_bfloat16 l1 = __float2bfloat16_rn(x1 - __bfloat162float(h1));
-    hi = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
-    lo = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+    const __nv_bfloat162 h = __floats2bfloat162_rn(x0, x1);
+    const float2 r = csub(make_float2(x0, x1), __bfloat1622float2(h));
+    const __nv_bfloat162 l = __floats2bfloat162_rn(r.x, r.y);
+    hi = *reinterpret_cast<const uint32_t *>(&h);
+    lo = *reinterpret_cast<const uint32_t *>(&l);
 }
 
 // Shared state of a block's tensor-core stages.
@@ -216,6 +218,134 @@ __device__ __forceinline__ void tc_dft16(float2 (&a)[16], const TcCtx &ctx)
 #pragma unroll
     for (int k = 0; k < 16; ++k) a[k] = make_float2(r[k], r[16 + k]);
     tc_fence_before(); // these reads precede the next batch of MMAs
+}
+
+// ---------------------------------------------------------------------------
+// Radix-16 stage on the tensor cores for lines of 512 points held 32 per
+// thread (plan 32 × 16: radix-32 butterflies in FP32, then the radix-16 stage
+// here, which is the last one).  Each thread owns two butterflies (rows), so
+// a warpgroup of 128 threads forms two 128-row A operands.  Warpgroups work
+// independently: each writes its operand rows, meets only its own 128
+// threads at a named barrier, has one elected thread issue its MMAs and
+// commit them to its own mbarrier, and then every thread waits on that
+// mbarrier and reads its two accumulator rows back.  TMEM columns
+// [64·g, 64·g + 64) belong to warpgroup g.
+
+// Named barrier over the 128 threads of warpgroup g (id 0 is __syncthreads).
+__device__ __forceinline__ void wg_barrier(int g)
+{
+    asm volatile("bar.sync %0, 128;" ::"r"(1 + g) : "memory");
+}
+
+// 64 consecutive FP32 columns of this thread's TMEM lane (one wait).
+__device__ __forceinline__ void tmem_ld64(uint32_t taddr, float (&r)[64])
+{
+    uint32_t u[64];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x64.b32 "
+                 "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                 "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,"
+                 "%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,%44,%45,%46,%47,"
+                 "%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63}, [%64];"
+                 : "=r"(u[0]), "=r"(u[1]), "=r"(u[2]), "=r"(u[3]), "=r"(u[4]), "=r"(u[5]), "=r"(u[6]),
+                   "=r"(u[7]), "=r"(u[8]), "=r"(u[9]), "=r"(u[10]), "=r"(u[11]), "=r"(u[12]), "=r"(u[13]),
+                   "=r"(u[14]), "=r"(u[15]), "=r"(u[16]), "=r"(u[17]), "=r"(u[18]), "=r"(u[19]),
+                   "=r"(u[20]), "=r"(u[21]), "=r"(u[22]), "=r"(u[23]), "=r"(u[24]), "=r"(u[25]),
+                   "=r"(u[26]), "=r"(u[27]), "=r"(u[28]), "=r"(u[29]), "=r"(u[30]), "=r"(u[31]),
+                   "=r"(u[32]), "=r"(u[33]), "=r"(u[34]), "=r"(u[35]), "=r"(u[36]), "=r"(u[37]),
+                   "=r"(u[38]), "=r"(u[39]), "=r"(u[40]), "=r"(u[41]), "=r"(u[42]), "=r"(u[43]),
+                   "=r"(u[44]), "=r"(u[45]), "=r"(u[46]), "=r"(u[47]), "=r"(u[48]), "=r"(u[49]),
+                   "=r"(u[50]), "=r"(u[51]), "=r"(u[52]), "=r"(u[53]), "=r"(u[54]), "=r"(u[55]),
+                   "=r"(u[56]), "=r"(u[57]), "=r"(u[58]), "=r"(u[59]), "=r"(u[60]), "=r"(u[61]),
+                   "=r"(u[62]), "=r"(u[63])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 64; ++i) r[i] = __uint_as_float(u[i]);
+}
+
+struct Tc32Ctx {
+    unsigned char *op;            // operand rows: [warpgroup][butterfly b][hi, lo] × 8 KiB
+    const unsigned char *f_hi[2]; // [forward, inverse] 32×32 BF16 DFT matrices
+    const unsigned char *f_lo[2];
+    uint32_t tmem;                // TMEM base (64 columns per warpgroup)
+    uint64_t *bar;                // one MMA completion barrier per warpgroup
+    int *abort;                   // shared flag set on a timed-out wait
+    int *status;                  // device status word
+};
+
+constexpr int kTcOpBytes = 128 * kTcRowBytes; // one 128-row BF16 operand (8 KiB)
+
+// Last stage (radix 16, Ns = 32) of a 512-point line, v[m] = x[t + 16·m]
+// on entry (the exchanged radix-32 outputs) and out[t + 16·m] on exit, with
+// the stage's twiddles w_512^{r·j} applied in FP32 first.  `nphase` counts
+// this warpgroup's completed MMA batches (identical in all its threads).
+template <bool INV>
+__device__ __forceinline__ void tc32_last_stage(float2 (&v)[32], int t, const float2 *__restrict__ tw,
+                                                const Tc32Ctx &c, uint32_t &nphase)
+{
+    constexpr int TL = 16, NB = 2;
+    const int tid = threadIdx.x, g = tid >> 7, rl = tid & 127;
+    const unsigned char *fh = c.f_hi[INV ? 1 : 0];
+    const unsigned char *fl = c.f_lo[INV ? 1 : 0];
+    // Butterfly 0's MMAs run while butterfly 1's operand rows are formed.
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+        const int j = t + b * TL; // butterfly j < Ns = 32: twiddle exponent r·j
+        float2 a[16];
+        a[0] = v[b];
+#pragma unroll
+        for (int r = 1; r < 16; ++r) {
+            const float2 w = tw[r * j];
+            a[r] = INV ? cmulc(v[b + r * NB], w) : cmul(v[b + r * NB], w);
+        }
+        uint32_t hi[16], lo[16];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            bf16_split2(a[2 * i].x, a[2 * i + 1].x, hi[i], lo[i]);         // Re
+            bf16_split2(a[2 * i].y, a[2 * i + 1].y, hi[8 + i], lo[8 + i]); // Im
+        }
+        unsigned char *oh = c.op + ((g * NB + b) * 2) * kTcOpBytes;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int off = tc_offset(rl, 8 * q);
+            *reinterpret_cast<uint4 *>(oh + off) = make_uint4(hi[4 * q], hi[4 * q + 1], hi[4 * q + 2], hi[4 * q + 3]);
+            *reinterpret_cast<uint4 *>(oh + kTcOpBytes + off) =
+                make_uint4(lo[4 * q], lo[4 * q + 1], lo[4 * q + 2], lo[4 * q + 3]);
+        }
+        fence_proxy_async_smem(); // operand rows before the tensor core reads them
+        tc_fence_before();
+        wg_barrier(g);
+        if (rl == 0) {
+            tc_fence_after();
+            const uint32_t d = c.tmem + (uint32_t)(64 * g + 32 * b);
+#pragma unroll
+            for (int ks = 0; ks < 2; ++ks) {
+                const int kofs = ks * 256; // two core matrices of K per step
+                const uint64_t ah = tc_smem_desc(oh + kofs, 128, 512);
+                const uint64_t al = tc_smem_desc(oh + kTcOpBytes + kofs, 128, 512);
+                const uint64_t bh = tc_smem_desc(fh + kofs, 128, 512);
+                const uint64_t bl = tc_smem_desc(fl + kofs, 128, 512);
+                tc_mma(d, ah, bh, ks > 0 ? 1u : 0u);
+                tc_mma(d, ah, bl, 1u);
+                tc_mma(d, al, bh, 1u);
+            }
+            if (b == NB - 1) tc_commit(&c.bar[g]); // completion of both butterflies' MMAs
+        }
+    }
+    if (!mbar_wait_bounded(&c.bar[g], nphase & 1u, 2000000000ull)) {
+        *c.abort = 1;
+        atomicExch(c.status, 5 /* PSOLVE_ERR_TIMEOUT */);
+    }
+    ++nphase;
+    tc_fence_after();
+    const int wq = (tid >> 5) & 3; // TMEM lanes 32·wq .. 32·wq + 31 for this warp
+    float r[64];
+    tmem_ld64(c.tmem + ((uint32_t)(32 * wq) << 16) + (uint32_t)(64 * g), r);
+#pragma unroll
+    for (int b = 0; b < NB; ++b)
+#pragma unroll
+        for (int k = 0; k < 16; ++k) v[b + k * NB] = make_float2(r[32 * b + k], r[32 * b + 16 + k]);
+    tc_fence_before(); // these reads precede the warpgroup's next MMAs
 }
 
 // Compile-time-plan line transform in which every radix-16 stage runs on the

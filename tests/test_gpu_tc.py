@@ -89,3 +89,19 @@ def test_tc_plan_stays_on_tensor_cores_after_autotune(lib, tmp_path, monkeypatch
     u = plan.execute(f).cpu().numpy().reshape(shape)
     err = oracle.rel_l2(u, oracle.solve(f.cpu().numpy().astype(np.float64).reshape(shape)))
     assert 1e-7 < err <= 1e-5  # tensor-core accuracy, not an FP32 result
+
+
+@pytest.mark.parametrize("cfg", ["1,1", "0,0", "3,3", "4,4", "3,4"])
+def test_tc_512_line_configurations(lib, monkeypatch, cfg):
+    """Every tensor-core variant of the 512-point y and x passes: plans of
+    radix-16 stages (16 points per thread: configurations 0, 1) and the
+    32 × 16 plan with its radix-16 stage on the tensor cores per warpgroup
+    (32 points per thread: 3 with one warpgroup per block, 4 with two)."""
+    monkeypatch.setenv("PSOLVE_TMA_NARROW", cfg)
+    oracle.build()
+    shape = (512, 512, 32)
+    f64 = wl.random_field(shape, seed=41)
+    u, f_in, names = _solve(shape, "f32_tc", f64)
+    assert names == ["zfwd", "yfwd_tc", "xdiv_tc", "yinv_tc", "zinv"]
+    err = oracle.rel_l2(u, oracle.solve(f_in.astype(np.float64)))
+    assert 1e-7 < err <= 1e-5, (cfg, err)
