@@ -287,15 +287,20 @@ def run_ours(args):
     f_pins = [f_pin, f_host.clone().pin_memory()]
     u_pins = [u_pin, torch.empty_like(f_pin).pin_memory()]
     streams = [torch.cuda.Stream(dev), torch.cuda.Stream(dev)]
-    for k in range(2):
-        plan.execute_host_async(f_pins[k], u_pins[k], streams[k])
-    torch.cuda.synchronize(dev)
-    barrier()
-    h0 = time.perf_counter()
-    for k in range(e2e_steps):
+    for k in range(4):
         plan.execute_host_async(f_pins[k % 2], u_pins[k % 2], streams[k % 2])
     torch.cuda.synchronize(dev)
-    e2e_s = (time.perf_counter() - h0) / e2e_steps
+    barrier()
+    # three timed runs of e2e_steps steps each; the median run is reported
+    # (the host link is shared with the machine's other GPUs' traffic)
+    runs = []
+    for _ in range(3):
+        h0 = time.perf_counter()
+        for k in range(e2e_steps):
+            plan.execute_host_async(f_pins[k % 2], u_pins[k % 2], streams[k % 2])
+        torch.cuda.synchronize(dev)
+        runs.append((time.perf_counter() - h0) / e2e_steps)
+    e2e_s = sorted(runs)[1]
     # the synchronous call, one step at a time, for reference
     plan.execute_host(f_pin, u_pin)
     h1 = time.perf_counter()
@@ -338,7 +343,7 @@ def run_ours(args):
         "min_traffic_frac": (8 * N / (ms_per_step * 1e-3) / 1e9) / peak,
         "e2e": {"value": ws * N / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 4 * N,
                 "d2h_bytes_per_step": 4 * N, "api": "psolve_execute_host_async, pinned buffers, 2 streams",
-                "sync_call_value": ws * N / e2e_sync_s},
+                "runs_ms": [round(r * 1e3, 4) for r in runs], "sync_call_value": ws * N / e2e_sync_s},
         "gpu_launches": plan.launches_per_solve * args.steps,
         "clocks": clocks,
     }
