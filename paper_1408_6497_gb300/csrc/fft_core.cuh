@@ -273,6 +273,15 @@ template <int SH = 4> struct MapStridedPad {
     int P, w;
     __device__ __forceinline__ int operator()(int p) const { return (p + (p >> SH)) * P + w; }
 };
+// [p][w] in exactly L·P slots (the tile buffer itself): row p trades places
+// with row p ^ 1 when bit SH of p is set.  With rows of 8 columns (half the
+// banks), the first stage's writes from neighbouring threads, 2^SH rows
+// apart, then land in opposite bank halves, and rows read together stay
+// adjacent pairs.
+template <int SH> struct MapStridedSwz {
+    int P, w;
+    __device__ __forceinline__ int operator()(int p) const { return (p ^ ((p >> SH) & 1)) * P + w; }
+};
 struct MapRow { // [w][p], one padded row per line (z passes)
     int base;
     __device__ __forceinline__ int operator()(int p) const { return base + p + (p >> 4); }

@@ -144,7 +144,8 @@ __global__ void __launch_bounds__(TmaShape<L, CFG>::NT, TmaShape<L, CFG>::MINB)
     long long tile = blockIdx.x;
     if (tid == 0 && tile < ntiles) issue(tile, buf0, &bar[0]);
 
-    const MapStrided map{W, w};
+    // exchanges in the tile buffer: rows swizzled, no spare space there
+    const MapStridedSwz<(ct_radix(L, 0, E) >= 32 ? 5 : (ct_radix(L, 0, E) >= 16 ? 4 : 3))> map{W, w};
     // spare row every R0 rows, R0 = the radix of the first stage
     constexpr int PADSH = ct_radix(L, 0, E) >= 32 ? 5 : 4;
     const MapStridedPad<PADSH> xmap{W, w};
