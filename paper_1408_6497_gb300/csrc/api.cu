@@ -103,6 +103,7 @@ bool make_line_plan(int L, LinePlan &p, int order = 0, int e3cap = 3)
         p.twstep[s] = L / (ns * rad[s]);
         ns *= rad[s];
     }
+    line_plan_finish(p);
     return true;
 }
 
@@ -138,6 +139,7 @@ bool make_line_plan_E(int L, int E, LinePlan &p)
         p.twstep[s] = L / (ns * rad[s]);
         ns *= rad[s];
     }
+    line_plan_finish(p);
     return true;
 }
 

@@ -101,10 +101,13 @@ __global__ void __launch_bounds__(kBatchThreads, PSOLVE_BATCH_MINB) k_batched(co
         case 16: run_item<T, 16>(sg, tile, f, u, smraw); break;
         default: break;
         }
-        // Publish this tile: every thread's stores, then one release count.
-        __threadfence();
+        // Publish this tile: the barrier orders every thread's stores before
+        // thread 0's fence (cumulative at GPU scope), then one count.
         __syncthreads();
-        if (threadIdx.x == 0) atomicAdd(&done[s_seg], 1);
+        if (threadIdx.x == 0) {
+            __threadfence();
+            atomicAdd(&done[s_seg], 1);
+        }
     }
 }
 

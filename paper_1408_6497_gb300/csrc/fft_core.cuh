@@ -258,7 +258,17 @@ struct LinePlan {
     int radix[kMaxStages];      // R_s
     int ns[kMaxStages];         // Ns before stage s
     int twstep[kMaxStages];     // L / (Ns·R): twiddle index step
+    unsigned nsmag[kMaxStages]; // ceil(2^32 / Ns) for Ns >= 2: j / Ns = umulhi(j, nsmag), exact while j·Ns < 2^32
 };
+
+// Fill the division multipliers of a plan whose ns[] are set.
+inline void line_plan_finish(LinePlan &p)
+{
+    for (int s = 0; s < p.nst; ++s)
+        p.nsmag[s] = p.ns[s] >= 2 ? (unsigned)(((1ull << 32) + (unsigned long long)p.ns[s] - 1) /
+                                               (unsigned long long)p.ns[s])
+                                  : 0u;
+}
 
 // Index map of a line's point p into the shared exchange buffer.
 struct MapStrided { // [p][w], pitch P: lines side by side (y and x passes)
@@ -288,7 +298,7 @@ struct MapRow { // [w][p], one padded row per line (z passes)
 };
 
 template <int R, bool INV, bool LAST, int E, typename C, typename Map>
-__device__ __forceinline__ void fft_stage(C (&v)[E], int t, int TL, int Ns, int twstep,
+__device__ __forceinline__ void fft_stage(C (&v)[E], int t, int TL, int Ns, unsigned nsmag, int twstep,
                                           const C *__restrict__ tw, C *sm, const Map &map,
                                           bool active)
 {
@@ -296,7 +306,8 @@ __device__ __forceinline__ void fft_stage(C (&v)[E], int t, int TL, int Ns, int 
 #pragma unroll
     for (int b = 0; b < NB; ++b) {
         const int j = t + b * TL;
-        const int jm = j % Ns;
+        // j mod Ns by a multiply-high (lines are far shorter than 2^16 points)
+        const int jm = Ns > 1 ? j - (int)__umulhi((unsigned)j, nsmag) * Ns : 0;
         C a[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) a[r] = v[b + r * NB];
@@ -325,25 +336,25 @@ __device__ __forceinline__ void fft_stage(C (&v)[E], int t, int TL, int Ns, int 
 template <int R, int E> struct RadixOk { static constexpr bool value = (E % R) == 0; };
 
 template <bool INV, bool LAST, int E, typename C, typename Map>
-__device__ __forceinline__ void fft_stage_dispatch(int R, C (&v)[E], int t, int TL, int Ns, int twstep,
+__device__ __forceinline__ void fft_stage_dispatch(int R, C (&v)[E], int t, int TL, int Ns, unsigned nsmag, int twstep,
                                                    const C *__restrict__ tw, C *sm, const Map &map,
                                                    bool active)
 {
     switch (R) {
     case 16:
-        if constexpr (RadixOk<16, E>::value) fft_stage<16, INV, LAST>(v, t, TL, Ns, twstep, tw, sm, map, active);
+        if constexpr (RadixOk<16, E>::value) fft_stage<16, INV, LAST>(v, t, TL, Ns, nsmag, twstep, tw, sm, map, active);
         break;
     case 8:
-        if constexpr (RadixOk<8, E>::value) fft_stage<8, INV, LAST>(v, t, TL, Ns, twstep, tw, sm, map, active);
+        if constexpr (RadixOk<8, E>::value) fft_stage<8, INV, LAST>(v, t, TL, Ns, nsmag, twstep, tw, sm, map, active);
         break;
     case 4:
-        if constexpr (RadixOk<4, E>::value) fft_stage<4, INV, LAST>(v, t, TL, Ns, twstep, tw, sm, map, active);
+        if constexpr (RadixOk<4, E>::value) fft_stage<4, INV, LAST>(v, t, TL, Ns, nsmag, twstep, tw, sm, map, active);
         break;
     case 3:
-        if constexpr (RadixOk<3, E>::value) fft_stage<3, INV, LAST>(v, t, TL, Ns, twstep, tw, sm, map, active);
+        if constexpr (RadixOk<3, E>::value) fft_stage<3, INV, LAST>(v, t, TL, Ns, nsmag, twstep, tw, sm, map, active);
         break;
     case 2:
-        if constexpr (RadixOk<2, E>::value) fft_stage<2, INV, LAST>(v, t, TL, Ns, twstep, tw, sm, map, active);
+        if constexpr (RadixOk<2, E>::value) fft_stage<2, INV, LAST>(v, t, TL, Ns, nsmag, twstep, tw, sm, map, active);
         break;
     default:
         break;
@@ -359,9 +370,9 @@ __device__ __forceinline__ void line_fft(C (&v)[E], int t, const LinePlan &pl,
     for (int s = 0; s < pl.nst; ++s) {
         const int R = pl.radix[s];
         if (s + 1 == pl.nst) {
-            fft_stage_dispatch<INV, true>(R, v, t, pl.TL, pl.ns[s], pl.twstep[s], tw, sm, map, active);
+            fft_stage_dispatch<INV, true>(R, v, t, pl.TL, pl.ns[s], pl.nsmag[s], pl.twstep[s], tw, sm, map, active);
         } else {
-            fft_stage_dispatch<INV, false>(R, v, t, pl.TL, pl.ns[s], pl.twstep[s], tw, sm, map, active);
+            fft_stage_dispatch<INV, false>(R, v, t, pl.TL, pl.ns[s], pl.nsmag[s], pl.twstep[s], tw, sm, map, active);
             __syncthreads();
             if (active) {
 #pragma unroll

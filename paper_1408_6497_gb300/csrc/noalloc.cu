@@ -89,6 +89,7 @@ bool line_plan(int L, LinePlan &p)
         p.twstep[s] = L / (ns * rad[s]);
         ns *= rad[s];
     }
+    line_plan_finish(p);
     return true;
 }
 
