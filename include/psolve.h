@@ -70,8 +70,13 @@ typedef struct psolve_plan psolve_plan;
  * be 2^a·3^b, even, 4 <= n <= 2048.  Allocates the plan's twiddle tables
  * (computed on the device in FP64) and status word on the current device.
  * The spectrum is formed inside u itself, so no workspace of the grid's
- * size is allocated.  On success *out owns the plan; release it with
- * psolve_destroy.  On failure *out is set to NULL. */
+ * size is allocated, except for FP32 grids whose x lines lie 4 MiB or more
+ * apart (ny·(nz/2)·8 bytes, e.g. 1024³): their plans also own a spectrum
+ * buffer of the grid's size (nx·ny·nz floats per grid), in which the
+ * spectrum is kept in an x-split order that serves the x transform better;
+ * if that allocation fails the plan keeps the in-place layout.  On success
+ * *out owns the plan; release it with psolve_destroy.  On failure *out is
+ * set to NULL. */
 psolve_status psolve_plan_create(int nx, int ny, int nz, int dtype, int batch,
                                  psolve_plan **out);
 

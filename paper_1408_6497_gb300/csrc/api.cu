@@ -42,6 +42,13 @@ constexpr unsigned kMagic = 0x50534F4Cu; // "PSOL"
 constexpr size_t kSmemCap = 200 * 1024;
 
 // Instances of equal dimensions laid out back to back at `stride` elements.
+// x-split factor of the spectrum layout (spec_row) for grids whose x lines
+// are at least kXSplitStride bytes apart in the natural layout (measured on
+// GB300: at 1024³, 4 MiB apart, the x pass drops from 3.47 to 2.36 ms while
+// the y and z passes lose 0.5 ms; at 512³, 1 MiB apart, it is a loss).
+constexpr int kXSplit = 4;
+constexpr double kXSplitStride = 4.0 * 1048576.0;
+
 struct Group {
     int nx, ny, nz, M;
     int count;
@@ -52,6 +59,7 @@ struct Group {
     int cfg_y, cfg_x;    // TMA configuration of the y / x pass (-1: per-tile kernel)
     int fused;           // z and y passes fused per plane through L2: cluster size, 0 = off
     int zbulk;           // z passes by the persistent bulk-copy kernel (1) or per-tile blocks (0)
+    int xs;              // x-split factor of the spectrum layout when every pass can use it (1: natural)
 };
 
 bool factor23(int n, int &a, int &b)
@@ -213,6 +221,7 @@ struct psolve_plan {
     std::vector<size_t> inst_off;
     size_t total;
     void *tables;
+    void *xsbuf; // spectrum in the x-split layout (plans that use it): the z passes go f -> xsbuf -> u
     int *status;
     void *stage;
     size_t stage_bytes;
@@ -307,6 +316,7 @@ void release(psolve_plan *p)
     if (p->tables) cudaFree(p->tables);
     if (p->status) cudaFree(p->status);
     if (p->stage) cudaFree(p->stage);
+    if (p->xsbuf) cudaFree(p->xsbuf);
     for (int i = 0; i < 2; ++i) {
         if (p->astage[i]) cudaFree(p->astage[i]);
         if (p->aev[i]) cudaEventDestroy(p->aev[i]);
@@ -589,6 +599,7 @@ psolve_status build_plan(const std::vector<int> &nx, const std::vector<int> &ny,
     p->tables = nullptr;
     p->status = nullptr;
     p->stage = nullptr;
+    p->xsbuf = nullptr;
     p->stage_bytes = 0;
     p->astage[0] = p->astage[1] = nullptr;
     p->aev[0] = p->aev[1] = nullptr;
@@ -681,6 +692,15 @@ psolve_status build_plan(const std::vector<int> &nx, const std::vector<int> &ny,
                           ? 1
                           : 0;
         }
+        {
+            // x-split spectrum layout (spec_row), used by solves whose passes
+            // all support it; PSOLVE_XSPLIT = 1 keeps the natural layout, 2..16
+            // asks for that factor
+            const char *xe = std::getenv("PSOLVE_XSPLIT");
+            const double xstride = (double)g.ny * g.M * csize(dtype);
+            const int G = xe ? std::atoi(xe) : (xstride >= kXSplitStride ? kXSplit : 1);
+            g.xs = (G == 2 || G == 4 || G == 8 || G == 16) ? G : 1;
+        }
         g.fused = 0;
         if (uniform && dtype == PSOLVE_F32 && fused_supported(g.M, g.ny) && g.pz.E == 16 && g.py.E == 16) {
             // Off by default (measured slower than the separate TMA passes on
@@ -711,6 +731,14 @@ psolve_status build_plan(const std::vector<int> &nx, const std::vector<int> &ny,
         g.cfg_x = pick(p->tma_narrow_x, g.nx, true);
     }
     apply_tuning_cache(p.get());
+    {
+        bool want_xs = false;
+        for (const auto &g : p->groups) want_xs = want_xs || (g.xs > 1 && g.zbulk);
+        if (want_xs && dtype != PSOLVE_F64 && cudaMalloc(&p->xsbuf, p->total * rsize(dtype)) != cudaSuccess) {
+            p->xsbuf = nullptr; // natural layout in u instead
+            cudaGetLastError();
+        }
+    }
     e = cudaMalloc(&p->tables, tcount * csize(dtype));
     if (e != cudaSuccess) {
         p->tables = nullptr;
@@ -790,8 +818,32 @@ bool encode_map(CUtensorMap *m, void *base, uint64_t d0, uint64_t d1, uint64_t d
 }
 
 
+bool encode_map4(CUtensorMap *m, void *base, const uint64_t (&d)[4], const uint32_t (&b)[4])
+{
+    auto fn = tensor_map_encoder();
+    if (!fn) return false;
+    cuuint64_t dims[4] = {d[0], d[1], d[2], d[3]};
+    cuuint64_t strides[3] = {d[0] * 8, d[0] * d[1] * 8, d[0] * d[1] * d[2] * 8};
+    cuuint32_t box[4] = {b[0], b[1], b[2], b[3]};
+    cuuint32_t es[4] = {1, 1, 1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_INT64, 4, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// x-split factor a solve of group g uses: every pass must be one that knows
+// the layout (bulk z passes, TMA y/x passes), the spectrum stays on the
+// device, and G divides nx and the x line's threads.
+int xs_factor(const psolve_plan *p, const Group &g, bool host_io)
+{
+    if (!p->xsbuf || g.xs <= 1 || host_io || g.fused > 0 || !g.zbulk || g.cfg_y < 0 || g.cfg_x < 0) return 1;
+    if (g.nx % g.xs != 0 || tma_threads(g.nx, g.cfg_x) / tma_columns(g.nx, g.cfg_x) % g.xs != 0) return 1;
+    if ((g.nx < 256 ? g.nx : 256) % g.xs != 0) return 1;
+    return g.xs;
+}
+
 template <typename T>
-psolve_status run_tma_pass(const psolve_plan *p, const Group &g, T *ui, int kind, cudaStream_t s)
+psolve_status run_tma_pass(const psolve_plan *p, const Group &g, T *ui, int kind, cudaStream_t s, int G = 1)
 {
     if constexpr (sizeof(T) != 4) {
         return fail(PSOLVE_ERR_INTERNAL, "TMA pass is FP32 only");
@@ -801,11 +853,19 @@ psolve_status run_tma_pass(const psolve_plan *p, const Group &g, T *ui, int kind
         const int W = tma_columns(L, narrow);
         const int boxr = L < 256 ? L : 256;
         CUtensorMap map;
-        const bool ok = kind == 2
-                            ? encode_map(&map, ui, (uint64_t)g.M, (uint64_t)g.ny, (uint64_t)g.nx * g.count,
-                                         (uint32_t)W, 1u, (uint32_t)boxr)
-                            : encode_map(&map, ui, (uint64_t)g.M, (uint64_t)g.ny, (uint64_t)g.nx * g.count,
-                                         (uint32_t)W, (uint32_t)boxr, 1u);
+        bool ok;
+        if (G > 1) {
+            // x-split layout: (M, G, ny, planes / G)
+            const uint64_t d[4] = {(uint64_t)g.M, (uint64_t)G, (uint64_t)g.ny, (uint64_t)g.nx * g.count / G};
+            const uint32_t bx[4] = {(uint32_t)W, (uint32_t)G, 1u, (uint32_t)(boxr / G)};
+            const uint32_t by[4] = {(uint32_t)W, 1u, (uint32_t)boxr, 1u};
+            ok = encode_map4(&map, ui, d, kind == 2 ? bx : by);
+        } else {
+            ok = kind == 2 ? encode_map(&map, ui, (uint64_t)g.M, (uint64_t)g.ny, (uint64_t)g.nx * g.count,
+                                        (uint32_t)W, 1u, (uint32_t)boxr)
+                           : encode_map(&map, ui, (uint64_t)g.M, (uint64_t)g.ny, (uint64_t)g.nx * g.count,
+                                        (uint32_t)W, (uint32_t)boxr, 1u);
+        }
         if (!ok) return fail(PSOLVE_ERR_CUDA, "cuTensorMapEncodeTiled failed");
         TmaArgs a{};
         a.data = reinterpret_cast<float2 *>(ui);
@@ -819,6 +879,7 @@ psolve_status run_tma_pass(const psolve_plan *p, const Group &g, T *ui, int kind
         a.coef = (float)(1.0 / (4.0 * M_PI * M_PI * ((double)g.nx * g.ny * g.nz)));
         a.status = p->status;
         a.tc = p->dtype == PSOLVE_F32_TC ? 1 : 0;
+        a.G = G;
         if (narrow == 2 && kind == 2 && !make_line_plan_E(g.nx, 8, a.pl_x))
             return fail(PSOLVE_ERR_INTERNAL, "no 8-point plan for the x line");
         long long work = a.main_tiles;
@@ -835,7 +896,7 @@ psolve_status run_tma_pass(const psolve_plan *p, const Group &g, T *ui, int kind
 // of a group with its current tile choices.
 template <typename T>
 psolve_status launch_pass(const psolve_plan *p, const Group &g, int kind, const T *fi, T *ui, cudaStream_t s,
-                          bool force_runtime = false, T *zout = nullptr, bool host_io = false)
+                          bool force_runtime = false, T *zout = nullptr, bool host_io = false, int G = 1)
 {
     using C = typename cplx_of<T>::type;
     const C *tab = reinterpret_cast<const C *>(p->tables);
@@ -853,6 +914,8 @@ psolve_status launch_pass(const psolve_plan *p, const Group &g, int kind, const 
             zb.tw = tab + g.tw_z;
             zb.post = tab + g.post;
             zb.status = p->status;
+            zb.ny = g.ny;
+            zb.G = G;
             const long long ntiles = zb.rows / z_bulk_rows(g.M);
             const unsigned grid = (unsigned)std::min<long long>(ntiles, 2LL * p->num_sms);
             e = launch_z_bulk(zb, g.M, kind == 4, grid, s);
@@ -880,7 +943,7 @@ psolve_status launch_pass(const psolve_plan *p, const Group &g, int kind, const 
         return PSOLVE_OK;
     }
     if (kind == 1 || kind == 3) {
-        if (g.cfg_y >= 0) return run_tma_pass<T>(p, g, ui, kind == 1 ? 0 : 1, s);
+        if (g.cfg_y >= 0) return run_tma_pass<T>(p, g, ui, kind == 1 ? 0 : 1, s, G);
         SArgs<T> y{};
         y.data = ui;
         y.nplanes = (long long)g.count * g.nx;
@@ -898,7 +961,7 @@ psolve_status launch_pass(const psolve_plan *p, const Group &g, int kind, const 
         if (e != cudaSuccess) return cuda_fail(e, kind == 1 ? "y forward pass" : "y inverse pass");
         return PSOLVE_OK;
     }
-    if (g.cfg_x >= 0) return run_tma_pass<T>(p, g, ui, 2, s);
+    if (g.cfg_x >= 0) return run_tma_pass<T>(p, g, ui, 2, s, G);
     XArgs<T> x{};
     x.data = ui;
     x.batch = g.count;
@@ -990,8 +1053,14 @@ psolve_status run_group(const psolve_plan *p, const Group &g, const T *f, T *u, 
         }
         return PSOLVE_OK;
     }
+    // one layout for the five passes of this solve
+    const int G = sizeof(T) == 4 ? xs_factor(p, g, host_io) : 1;
+    // x-split solves keep their spectrum in the plan's own buffer: the layout
+    // change cannot be made in place
+    T *work = G > 1 ? reinterpret_cast<T *>(p->xsbuf) + g.off0 : ui;
     for (int kind = 0; kind < kPasses; ++kind) {
-        psolve_status st = launch_pass<T>(p, g, kind, fi, ui, s, false, kind == 4 ? uo : nullptr, host_io);
+        T *zo = kind == 4 ? (uo ? uo : (G > 1 ? ui : nullptr)) : nullptr;
+        psolve_status st = launch_pass<T>(p, g, kind, fi, work, s, false, zo, host_io, G);
         if (st != PSOLVE_OK) return st;
         if (ev) cudaEventRecord((*ev)[kind + 1], s);
     }

@@ -292,9 +292,9 @@ template <int SH> struct MapStridedSwz {
     int P, w;
     __device__ __forceinline__ int operator()(int p) const { return (p ^ ((p >> SH) & 1)) * P + w; }
 };
-struct MapRow { // [w][p], one padded row per line (z passes)
+template <int SH = 4> struct MapRow { // [w][p], one row per line with a spare slot every 2^SH (z passes)
     int base;
-    __device__ __forceinline__ int operator()(int p) const { return base + p + (p >> 4); }
+    __device__ __forceinline__ int operator()(int p) const { return base + p + (p >> SH); }
 };
 
 template <int R, bool INV, bool LAST, int E, typename C, typename Map>

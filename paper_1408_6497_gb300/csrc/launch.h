@@ -39,7 +39,20 @@ struct TmaArgs {
     int *status;           // device status word
     LinePlan pl_x;         // run-time plan of the x line (packed-column pairs)
     int tc;                // radix-16 stages on the tensor cores (cfg 0 and 1 only)
+    int G;                 // x-split factor of the spectrum layout (1: natural; see
+                           // spec_row), the tensor map then 4D (M, G, ny, planes/G)
 };
+
+// Row (x, y) of the packed spectrum, x counted over all instances of a group
+// (x = instance·nx + x_local), in the x-split layout with factor G: rows are
+// ordered (x / G, y, x mod G), so the G rows of an x-group at one y are
+// adjacent.  A line along x then touches L/G separate places in memory
+// instead of L (fewer address translations per tile); G = 1 is the natural
+// (x, y) order.
+__host__ __device__ inline long long spec_row(long long x, long long y, int ny, int G)
+{
+    return ((x / G) * ny + y) * G + (x % G);
+}
 bool tma_supported(int L);
 // cfg 0: 64 KiB tiles, 16 points per thread, one 512-thread block per SM;
 // cfg 1: 32 KiB tiles, 16 points per thread, 256-thread blocks, two per SM;
@@ -62,6 +75,7 @@ struct ZBulkArgs {
     const float2 *tw;     // e^{-2πi j/M}
     const float2 *post;   // e^{-2πi k/nz}, k < M
     int *status;
+    int ny, G;            // spectrum rows in the x-split layout (spec_row; G = 1: natural)
 };
 bool z_bulk_supported(int M);
 int z_bulk_rows(int M);

@@ -111,7 +111,7 @@ __device__ __forceinline__ void zfwd_tile(const ZArgs<T> &a, const T *in, T *out
     }
     __syncthreads();
     const int LP = M + (M >> 4) + 1;
-    const MapRow map{w * LP};
+    const MapRow<> map{w * LP};
     line_fft_any<false, LC>(v, t, a.pl, stw, sx, map, active);
     // Z[k] -> X[k] needs Z[M-k]: exchange through shared memory.
     if (active) {
@@ -155,7 +155,7 @@ __device__ __forceinline__ void zinv_tile(const ZArgs<T> &a, const T *in, T *out
     for (int i = tid; i < M; i += blockDim.x) stw[i] = a.tw[i];
     C v[E];
     const int LP = M + (M >> 4) + 1;
-    const MapRow map{w * LP};
+    const MapRow<> map{w * LP};
     if (active) {
         const C *src = reinterpret_cast<const C *>(in) + row * M + t;
 #pragma unroll
@@ -234,11 +234,12 @@ __device__ __forceinline__ void ypass_tile(const SArgs<T> &a, T *data, long long
 // Lines 2q and 2q+1 of the block hold rows ky and (ny - ky) mod ny; block
 // `pidx` takes pairs pidx·(W/2) .. pidx·(W/2) + W/2 - 1.  All threads of the
 // block must call it (it synchronises).
+// G: x-split factor of the spectrum layout (1: natural; else TL % G == 0).
 template <typename T, int E, int LC, bool CG = false>
 __device__ __forceinline__ void xpair_block(T *data, int nx_rt, int ny, int M, long long sInst, long long npairs,
                                             T coef, const LinePlan &pl, int W, int TL, long long pidx, int t,
                                             int w, const typename cplx_of<T>::type *stw,
-                                            typename cplx_of<T>::type *sx)
+                                            typename cplx_of<T>::type *sx, int G = 1)
 {
     using C = typename cplx_of<T>::type;
     const int nx = LC > 0 ? LC : nx_rt;
@@ -254,7 +255,9 @@ __device__ __forceinline__ void xpair_block(T *data, int nx_rt, int ny, int M, l
     const long long b = active ? pair / per : 0;
     const int ky = active ? (int)(pair % per) : 0;
     const int row = side ? (ny - ky) % ny : ky;
-    C *base = reinterpret_cast<C *>(data) + b * sInst + (long long)row * M + (long long)t * sL;
+    // point x = t + m·TL of row `row`: spec_row(x, row) with x / G = t / G + m·TL / G
+    C *base = reinterpret_cast<C *>(data) + b * sInst + (long long)row * G * M +
+              ((long long)(t / G) * ny * G + t % G) * M;
     if (active) {
 #pragma unroll
         for (int m = 0; m < E; ++m) v[m] = ld_data<CG>(base + m * step);

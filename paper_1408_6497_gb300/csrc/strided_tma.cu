@@ -131,12 +131,20 @@ __global__ void __launch_bounds__(TmaShape<L, CFG>::NT, TmaShape<L, CFG>::MINB)
         mbar_expect_tx(b, S::TILE_BYTES);
 #pragma unroll
         for (int r = 0; r < S::NLOAD; ++r) {
+            // x-split layout (G > 1): 4D map (M, G, ny, planes / G); the box
+            // of an x line covers (W, G, 1, BOXR / G) and lands in shared
+            // memory in plain x order, exactly like the 3D box
             if (KIND == 2) {
                 const int y = (int)(rest % a.ny);
                 const long long inst = rest / a.ny;
-                tma_load_3d(dst + r * S::BOXR * W, &tmap, b, cb * W, y, (int)(inst * L + r * S::BOXR));
+                const int x0 = (int)(inst * L + r * S::BOXR);
+                if (a.G > 1) tma_load_4d(dst + r * S::BOXR * W, &tmap, b, cb * W, 0, y, x0 / a.G);
+                else tma_load_3d(dst + r * S::BOXR * W, &tmap, b, cb * W, y, x0);
             } else {
-                tma_load_3d(dst + r * S::BOXR * W, &tmap, b, cb * W, r * S::BOXR, (int)rest);
+                if (a.G > 1)
+                    tma_load_4d(dst + r * S::BOXR * W, &tmap, b, cb * W, (int)(rest % a.G), r * S::BOXR,
+                                (int)(rest / a.G));
+                else tma_load_3d(dst + r * S::BOXR * W, &tmap, b, cb * W, r * S::BOXR, (int)rest);
             }
         }
     };
@@ -228,11 +236,14 @@ __global__ void __launch_bounds__(TmaShape<L, CFG>::NT, TmaShape<L, CFG>::MINB)
                 constexpr int PAR = ct_exchanges(L, E) & 1;
                 line_fft_ct_db<true, L, 0, PAR>(v, t, stw, xbuf, cur, xmap, map);
             }
+            // point x = t + m·TL of line (y, col): row spec_row(x, y) (TL % G == 0)
             step = (long long)TL * a.ny * a.M;
-            base = a.data + inst * a.sInst + (long long)y * a.M + col + (long long)t * a.ny * a.M;
+            base = a.data + inst * a.sInst + (long long)y * a.G * a.M + col +
+                   ((long long)(t / a.G) * a.ny * a.G + t % a.G) * a.M;
         } else {
-            step = (long long)TL * a.M;
-            base = a.data + rest * (long long)a.ny * a.M + col + (long long)t * a.M;
+            // point y = t + m·TL of plane `rest`: row spec_row(rest, y)
+            step = (long long)TL * a.G * a.M;
+            base = a.data + ((rest / a.G) * a.ny * a.G + (long long)t * a.G + rest % a.G) * a.M + col;
         }
         if (active && !(KIND == 2 && col == 0)) {
 #pragma unroll
@@ -247,7 +258,7 @@ __global__ void __launch_bounds__(TmaShape<L, CFG>::NT, TmaShape<L, CFG>::MINB)
         for (long long p = blockIdx.x; p < npt; p += gridDim.x) {
             xpair_block<float, E, (E == 16 || E == 32 ? L : 0)>(reinterpret_cast<float *>(a.data), L, a.ny, a.M,
                                                                  a.sInst, a.npairs, a.coef, a.pl_x, W, TL, p, t,
-                                                                 w, stw, buf0);
+                                                                 w, stw, buf0, a.G);
             __syncthreads();
         }
     }

@@ -19,17 +19,21 @@ namespace {
 
 constexpr uint64_t kZWaitNs = 2000000000ull;
 
+// M = 256: 16 points per thread (radix 16 × 16), 256 threads; M = 512: 32
+// points per thread (radix 32 × 16: one exchange instead of two), 128
+// threads.  Both: 32 KiB tiles, two blocks per SM.
 template <int M> struct ZShape {
-    static constexpr int E = 16;
+    static constexpr int E = M >= 512 ? 32 : 16;
     static constexpr int TL = M / E;
-    static constexpr int NT = 256;
+    static constexpr int NT = M >= 512 ? 128 : 256;
+    static constexpr int SH = E >= 32 ? 5 : 4;              // exchange padding period
     static constexpr int W = NT / TL;                       // rows per tile
     static constexpr int LP = M + (M >> 4) + 1;             // padded row pitch (complex)
     static constexpr uint32_t TILE_BYTES = (uint32_t)(W * M * 8);
 };
 
 template <int M, bool INV>
-__global__ void __launch_bounds__(256, 2) k_z_bulk(ZBulkArgs a)
+__global__ void __launch_bounds__(ZShape<M>::NT, 2) k_z_bulk(ZBulkArgs a)
 {
     using S = ZShape<M>;
     constexpr int E = S::E, TL = S::TL, W = S::W;
@@ -63,7 +67,7 @@ __global__ void __launch_bounds__(256, 2) k_z_bulk(ZBulkArgs a)
     };
     long long tile = blockIdx.x;
     if (tid == 0 && tile < ntiles) issue(tile, buf0, &bar[0]);
-    const MapRow xm{w * S::LP};
+    const MapRow<S::SH> xm{w * S::LP};
 
     for (int k = 0; tile < ntiles; ++k, tile += gridDim.x) {
         float2 *cur = (k & 1) ? buf1 : buf0;
@@ -82,6 +86,8 @@ __global__ void __launch_bounds__(256, 2) k_z_bulk(ZBulkArgs a)
         __syncthreads();
         if (*abort_flag) break;
 
+        // forward: tile rows are rows of f (natural order); inverse: rows of
+        // the spectrum (x-split order), written back to their natural row
         const long long row = tile * W + w;
         const float2 *rowp = cur + w * M;
         float2 v[E];
@@ -93,7 +99,8 @@ __global__ void __launch_bounds__(256, 2) k_z_bulk(ZBulkArgs a)
 #pragma unroll
             for (int m = 0; m < E; ++m) xb[xm(t + m * TL)] = v[m];
             __syncthreads();
-            float2 *dst = reinterpret_cast<float2 *>(a.spec) + row * M;
+            const long long srow = a.G > 1 ? spec_row(row / a.ny, row % a.ny, a.ny, a.G) : row;
+            float2 *dst = reinterpret_cast<float2 *>(a.spec) + srow * M;
 #pragma unroll
             for (int m = 0; m < E; ++m) {
                 const int kk = t + m * TL;
@@ -122,7 +129,12 @@ __global__ void __launch_bounds__(256, 2) k_z_bulk(ZBulkArgs a)
                 }
             }
             line_fft_ct_from<true, M, 0>(v, t, stw, xb, xm, true);
-            float2 *dst = reinterpret_cast<float2 *>(a.real_out + row * (2 * M)) + t;
+            long long nrow = row;
+            if (a.G > 1) {
+                const long long q = row / a.G;
+                nrow = ((q / a.ny) * a.G + row % a.G) * a.ny + q % a.ny;
+            }
+            float2 *dst = reinterpret_cast<float2 *>(a.real_out + nrow * (2 * M)) + t;
 #pragma unroll
             for (int m = 0; m < E; ++m) dst[m * TL] = v[m];
         }
@@ -145,7 +157,7 @@ template <int M, bool INV> cudaError_t run(const ZBulkArgs &a, unsigned grid, cu
 
 bool z_bulk_supported(int M) { return M == 256 || M == 512; }
 
-int z_bulk_rows(int M) { return 256 / (M / 16); }
+int z_bulk_rows(int M) { return M >= 512 ? 128 / (M / 32) : 256 / (M / 16); }
 
 size_t z_bulk_smem(int M)
 {

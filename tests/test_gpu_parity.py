@@ -106,6 +106,44 @@ def test_fused_zy_batch_fp32(monkeypatch):
         assert oracle.rel_l2(u[b], oracle.solve(f_in[b].astype(np.float64))) <= TOL["f32"]
 
 
+# The x-split spectrum layout (rows ordered (x / G, y, x mod G) in the plan's
+# own spectrum buffer): forced on shapes that take the bulk z passes and the
+# TMA y/x passes, single and uniform-batch plans, in and out of place.
+XS_SHAPES = [(256, 256, 512), (512, 256, 1024), (1024, 256, 512), (256, 512, 512)]
+
+
+@pytest.mark.parametrize("G", ["2", "4", "8"])
+@pytest.mark.parametrize("shape", XS_SHAPES)
+def test_xsplit_layout_parity_fp32(shape, G, monkeypatch):
+    f64 = wl.random_field(shape, seed=900 + sum(shape))
+    f = torch.from_numpy(f64.astype(np.float32).ravel()).cuda()
+    monkeypatch.setenv("PSOLVE_XSPLIT", "1")
+    u_nat = Plan(shape, dtype="f32").execute(f)
+    monkeypatch.setenv("PSOLVE_XSPLIT", G)
+    free0 = torch.cuda.mem_get_info()[0]
+    plan = Plan(shape, dtype="f32")
+    # the plan owns a spectrum buffer of the grid's size
+    assert free0 - torch.cuda.mem_get_info()[0] >= f.numel() * 4
+    u = plan.execute(f)
+    plan.status()
+    ref = oracle.solve(f.cpu().numpy().astype(np.float64).reshape(shape))
+    assert oracle.rel_l2(u.cpu().numpy().reshape(shape), ref) <= TOL["f32"]
+    # same butterflies in another memory order: identical results
+    assert torch.equal(u, u_nat)
+    uu = f.clone()
+    plan.execute(uu, uu)  # in place: f and u are the same array
+    assert torch.equal(uu, u)
+
+
+def test_xsplit_layout_batch_fp32(monkeypatch):
+    monkeypatch.setenv("PSOLVE_XSPLIT", "4")
+    shape, B = (256, 256, 512), 3
+    f = np.stack([wl.random_field(shape, seed=60 + b) for b in range(B)])
+    u, f_in = gpu_solve(f, "f32", batch=B)
+    for b in range(B):
+        assert oracle.rel_l2(u[b], oracle.solve(f_in[b].astype(np.float64))) <= TOL["f32"]
+
+
 def test_config1_fp64_mode_sum_closed_form():
     w = wl.mode_sum()
     u, _ = gpu_solve(w.f, "f64")
