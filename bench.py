@@ -62,6 +62,31 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(dist, values, device):
+    """Element-wise maximum of `values` (floats) over all ranks; the values
+    themselves when there is no process group."""
+    if dist is None:
+        return [float(v) for v in values]
+    import torch
+    t = torch.tensor([float(v) for v in values], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t.cpu()]
+
+
+def job_value(ws: int, units_per_rank: float, ms_per_step: float) -> float:
+    """Whole-job throughput: every rank solves its own replica, so the job
+    does ws times the units of one rank in the slowest rank's time."""
+    return ws * units_per_rank / (ms_per_step * 1e-3)
+
+
+def emit(line: dict, rank: int) -> bool:
+    """Print the JSON line on rank 0 only; True if this rank printed."""
+    if rank != 0:
+        return False
+    print(json.dumps(line), flush=True)
+    return True
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -212,7 +237,7 @@ def run_reference(args):
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-    print(json.dumps(line), flush=True)
+    emit(line, rank)
     return 0
 
 
@@ -309,13 +334,10 @@ def run_ours(args):
     e2e_sync_s = (time.perf_counter() - h1) / 3
     barrier()
 
-    if dist is not None:
-        t = torch.tensor([el_ms, e2e_s], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        el_ms, e2e_s = float(t[0]), float(t[1])
+    el_ms, e2e_s, e2e_sync_s = max_over_ranks(dist, [el_ms, e2e_s, e2e_sync_s], dev)
 
     ms_per_step = el_ms / args.steps
-    value = ws * N / (ms_per_step * 1e-3)
+    value = job_value(ws, N, ms_per_step)
     avg = {k: v / max(1, nsol) for k, v in pass_ms.items()}
     top = max(avg, key=avg.get)
     peak, peak_kind = peaks()
@@ -324,6 +346,8 @@ def run_ours(args):
     traffic = recorded_traffic(top, N)
 
     if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
         return 0
     line = {
         "impl": "ours", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
@@ -358,7 +382,7 @@ def run_ours(args):
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                                 "sample": f"{reps} FP64 oracle solve(s) of the same source on a "
                                           f"{min(n, 256)}^3 grid, median {t:.2f} s"}
-    print(json.dumps(line), flush=True)
+    emit(line, rank)
     if dist is not None:
         dist.destroy_process_group()
     return 0

@@ -1,0 +1,69 @@
+"""Host-side logic of bench.py's multi-process path (replicas, no data-path
+collective): the max-over-ranks reduction and the whole-job value on two
+gloo ranks, rank-0-only output, and the reference arm's non-zero ranks."""
+import importlib.util
+import os
+import subprocess
+import sys
+
+import pytest
+import torch
+import torch.distributed as dist
+import torch.multiprocessing as mp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _bench():
+    spec = importlib.util.spec_from_file_location("bench_mod", os.path.join(ROOT, "bench.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+def _rank_main(rank, world, port, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        b = _bench()
+        ws, r, _ = b.dist_env()
+        # each rank timed its own replica: rank r took 10·(r+1) ms for 5 steps
+        el_ms, e2e_s = b.max_over_ranks(dist, [10.0 * (rank + 1), 0.001 * (2 - rank)], "cpu")
+        ms = el_ms / 5
+        printed = b.emit({"rank": r}, r)
+        out.put((rank, ws, r, el_ms, e2e_s, b.job_value(ws, 1000, ms), printed))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_max_and_value():
+    ctx = mp.get_context("spawn")
+    out = ctx.Queue()
+    port = 29500 + os.getpid() % 1000
+    procs = [ctx.Process(target=_rank_main, args=(r, 2, port, out)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = sorted(out.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for rank, ws, r, el_ms, e2e_s, value, printed in res:
+        assert (ws, r) == (2, rank)
+        assert el_ms == 20.0 and e2e_s == pytest.approx(0.002)  # the slowest rank's times
+        assert value == pytest.approx(2 * 1000 / (4.0e-3))       # both replicas over the max time
+        assert printed == (rank == 0)
+
+
+def test_max_over_ranks_without_group():
+    b = _bench()
+    assert b.max_over_ranks(None, [1, 2.5], "cpu") == [1.0, 2.5]
+    assert b.job_value(1, 512 ** 3, 1.0) == pytest.approx(512 ** 3 / 1e-3)
+
+
+def test_reference_arm_other_ranks_exit_without_work():
+    env = dict(os.environ, RANK="1", WORLD_SIZE="2", LOCAL_RANK="1")
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                        "--steps", "1", "--warmup", "0"], capture_output=True, text=True, env=env,
+                       timeout=120)
+    assert r.returncode == 0
+    assert r.stdout.strip() == ""
