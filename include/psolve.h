@@ -106,10 +106,11 @@ psolve_status psolve_execute_host(psolve_plan *plan, const void *f_host, void *u
 
 /* Asynchronous psolve_execute_host for pipelines: enqueue on `stream` and
  * return at once.  f is copied in and u copied out by the copy engines
- * (pinned buffers make these asynchronous).  The plan keeps two device
- * staging buffers and uses them in turn, each guarded by an event, so
- * consecutive calls issued on different streams overlap one solve's output
- * copy with the next one's input copy and kernels.  f_host and u_host must stay valid and unchanged
+ * (pinned buffers make these asynchronous).  The plan keeps three device
+ * staging buffers of the grid's size, allocated on first use and used in
+ * turn, each guarded by an event, so consecutive calls issued on different
+ * streams (three or more) overlap one solve's output copy with the next
+ * one's input copy and a third one's kernels.  f_host and u_host must stay valid and unchanged
  * until the work on `stream` completes; synchronise the streams to collect
  * u.  Calls for one plan must come from one host thread. */
 psolve_status psolve_execute_host_async(psolve_plan *plan, const void *f_host, void *u_host, void *stream);

@@ -41,7 +41,11 @@ psolve_status cuda_fail(cudaError_t e, const char *where)
 constexpr unsigned kMagic = 0x50534F4Cu; // "PSOL"
 constexpr size_t kSmemCap = 200 * 1024;
 
-// Instances of equal dimensions laid out back to back at `stride` elements.
+// Device staging buffers of psolve_execute_host_async, used in turn: three
+// let a pipeline of solves keep both directions of the host link busy while
+// a third solve computes.
+constexpr int kAsyncRing = 3;
+
 // x-split factor of the spectrum layout (spec_row) for grids whose x lines
 // are at least kXSplitStride bytes apart in the natural layout (measured on
 // GB300: at 1024³, 4 MiB apart, the x pass drops from 3.47 to 2.36 ms while
@@ -49,6 +53,7 @@ constexpr size_t kSmemCap = 200 * 1024;
 constexpr int kXSplit = 4;
 constexpr double kXSplitStride = 4.0 * 1048576.0;
 
+// Instances of equal dimensions laid out back to back at `stride` elements.
 struct Group {
     int nx, ny, nz, M;
     int count;
@@ -227,9 +232,9 @@ struct psolve_plan {
     size_t stage_bytes;
     // asynchronous host-buffer solves: two staging buffers used in turn, each
     // guarded by an event recorded after its last use
-    void *astage[2];
-    cudaEvent_t aev[2];
-    bool aev_used[2];
+    void *astage[kAsyncRing];
+    cudaEvent_t aev[kAsyncRing];
+    bool aev_used[kAsyncRing];
     unsigned aring;
     // persistent batched path (plans of unequal grids)
     bool batched;
@@ -317,7 +322,7 @@ void release(psolve_plan *p)
     if (p->status) cudaFree(p->status);
     if (p->stage) cudaFree(p->stage);
     if (p->xsbuf) cudaFree(p->xsbuf);
-    for (int i = 0; i < 2; ++i) {
+    for (int i = 0; i < kAsyncRing; ++i) {
         if (p->astage[i]) cudaFree(p->astage[i]);
         if (p->aev[i]) cudaEventDestroy(p->aev[i]);
     }
@@ -601,9 +606,11 @@ psolve_status build_plan(const std::vector<int> &nx, const std::vector<int> &ny,
     p->stage = nullptr;
     p->xsbuf = nullptr;
     p->stage_bytes = 0;
-    p->astage[0] = p->astage[1] = nullptr;
-    p->aev[0] = p->aev[1] = nullptr;
-    p->aev_used[0] = p->aev_used[1] = false;
+    for (int i = 0; i < kAsyncRing; ++i) {
+        p->astage[i] = nullptr;
+        p->aev[i] = nullptr;
+        p->aev_used[i] = false;
+    }
     p->aring = 0;
     p->profiling = false;
     p->batched = false;
@@ -1470,7 +1477,7 @@ psolve_status psolve_execute_host_async(psolve_plan *plan, const void *f_host, v
     DeviceGuard dg(plan->device);
     if (dg.err != cudaSuccess) return cuda_fail(dg.err, "select device");
     const size_t bytes = plan->total * rsize(plan->dtype);
-    const unsigned i = plan->aring++ & 1u;
+    const unsigned i = plan->aring++ % kAsyncRing;
     if (!plan->astage[i]) {
         if (cudaMalloc(&plan->astage[i], bytes) != cudaSuccess) {
             plan->astage[i] = nullptr;

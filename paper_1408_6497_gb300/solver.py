@@ -127,8 +127,8 @@ class Plan:
 
     def execute_host_async(self, f_host: torch.Tensor, u_host: torch.Tensor, stream=None) -> torch.Tensor:
         """Enqueue a host-buffer solve without waiting (pinned tensors go
-        straight across the host link); alternate streams to overlap
-        consecutive solves, then synchronise them."""
+        straight across the host link); rotate over three or more streams to
+        overlap consecutive solves, then synchronise them."""
         if f_host.numel() != self.total or u_host.numel() != self.total:
             raise ValueError(f"host tensors must hold {self.total} elements")
         with torch.cuda.device(self.device):
