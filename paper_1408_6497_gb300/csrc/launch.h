@@ -40,7 +40,8 @@ struct TmaArgs {
     LinePlan pl_x;         // run-time plan of the x line (packed-column pairs)
     int tc;                // radix-16 stages on the tensor cores (cfg 0 and 1 only)
     int G;                 // x-split factor of the spectrum layout (1: natural; see
-                           // spec_row), the tensor map then 4D (M, G, ny, planes/G)
+                           // spec_row); x lines then use a 4D map (M, G, ny, planes/G),
+                           // y lines a 3D one (G·M, ny, planes/G)
 };
 
 // Row (x, y) of the packed spectrum, x counted over all instances of a group

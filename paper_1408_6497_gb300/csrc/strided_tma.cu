@@ -131,8 +131,8 @@ __global__ void __launch_bounds__(TmaShape<L, CFG>::NT, TmaShape<L, CFG>::MINB)
         mbar_expect_tx(b, S::TILE_BYTES);
 #pragma unroll
         for (int r = 0; r < S::NLOAD; ++r) {
-            // x-split layout (G > 1): 4D map (M, G, ny, planes / G); the box
-            // of an x line covers (W, G, 1, BOXR / G) and lands in shared
+            // x-split layout (G > 1): x lines through a 4D map (M, G, ny,
+            // planes / G) whose box (W, G, 1, BOXR / G) lands in shared
             // memory in plain x order, exactly like the 3D box
             if (KIND == 2) {
                 const int y = (int)(rest % a.ny);
@@ -141,10 +141,10 @@ __global__ void __launch_bounds__(TmaShape<L, CFG>::NT, TmaShape<L, CFG>::MINB)
                 if (a.G > 1) tma_load_4d(dst + r * S::BOXR * W, &tmap, b, cb * W, 0, y, x0 / a.G);
                 else tma_load_3d(dst + r * S::BOXR * W, &tmap, b, cb * W, y, x0);
             } else {
-                if (a.G > 1)
-                    tma_load_4d(dst + r * S::BOXR * W, &tmap, b, cb * W, (int)(rest % a.G), r * S::BOXR,
-                                (int)(rest / a.G));
-                else tma_load_3d(dst + r * S::BOXR * W, &tmap, b, cb * W, r * S::BOXR, (int)rest);
+                // y lines: 3D either way; in the x-split layout the map's rows
+                // are G·M wide and the plane's x mod G selects the column block
+                const int c0 = a.G > 1 ? (int)(rest % a.G) * a.M + cb * W : cb * W;
+                tma_load_3d(dst + r * S::BOXR * W, &tmap, b, c0, r * S::BOXR, (int)(rest / a.G));
             }
         }
     };
