@@ -18,7 +18,7 @@
 #include "tma.cuh"
 
 #ifndef PSOLVE_BATCH_MINB
-#define PSOLVE_BATCH_MINB 2
+#define PSOLVE_BATCH_MINB 4
 #endif
 
 namespace psolve {
