@@ -1,5 +1,5 @@
-// Persistent z passes fed by 1D bulk copies, FP32 rows of M = 256 or 512
-// complex points (nz = 512 or 1024).
+// Persistent z passes fed by 1D bulk copies, FP32 rows of M = 64, 128, 256
+// or 512 complex points (nz = 128 … 1024).
 //
 // A tile is W consecutive rows (W·nz reals, contiguous in HBM), 32 KiB; one
 // cp.async.bulk brings tile i+1 into shared memory while tile i is being
@@ -19,9 +19,9 @@ namespace {
 
 constexpr uint64_t kZWaitNs = 2000000000ull;
 
-// M = 256: 16 points per thread (radix 16 × 16), 256 threads; M = 512: 32
-// points per thread (radix 32 × 16: one exchange instead of two), 128
-// threads.  Both: 32 KiB tiles, two blocks per SM.
+// M = 64, 128, 256: 16 points per thread (radix 16 × 4, 16 × 8, 16 × 16),
+// 256 threads; M = 512: 32 points per thread (radix 32 × 16: one exchange
+// instead of two), 128 threads.  All: 32 KiB tiles, two blocks per SM.
 template <int M> struct ZShape {
     static constexpr int E = M >= 512 ? 32 : 16;
     static constexpr int TL = M / E;
@@ -155,7 +155,7 @@ template <int M, bool INV> cudaError_t run(const ZBulkArgs &a, unsigned grid, cu
 
 } // namespace
 
-bool z_bulk_supported(int M) { return M == 256 || M == 512; }
+bool z_bulk_supported(int M) { return M == 64 || M == 128 || M == 256 || M == 512; }
 
 int z_bulk_rows(int M) { return M >= 512 ? 128 / (M / 32) : 256 / (M / 16); }
 
@@ -168,6 +168,8 @@ size_t z_bulk_smem(int M)
 
 cudaError_t launch_z_bulk(const ZBulkArgs &a, int M, bool inverse, unsigned grid, cudaStream_t s)
 {
+    if (M == 64) return inverse ? run<64, true>(a, grid, s) : run<64, false>(a, grid, s);
+    if (M == 128) return inverse ? run<128, true>(a, grid, s) : run<128, false>(a, grid, s);
     if (M == 256) return inverse ? run<256, true>(a, grid, s) : run<256, false>(a, grid, s);
     if (M == 512) return inverse ? run<512, true>(a, grid, s) : run<512, false>(a, grid, s);
     return cudaErrorInvalidValue;

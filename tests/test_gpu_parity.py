@@ -38,7 +38,8 @@ def gpu_solve(f64, prec, batch=1):
 
 SHAPES = [(4, 4, 4), (8, 6, 4), (6, 6, 6), (12, 24, 48), (16, 32, 64), (24, 32, 48), (96, 48, 24),
           (18, 54, 12), (4, 6, 8), (64, 64, 64), (128, 96, 24), (36, 12, 6), (48, 16, 256),
-          (2048, 4, 8), (4, 2048, 4), (8, 4, 2048), (162, 8, 18), (32, 32, 1024)]
+          (2048, 4, 8), (4, 2048, 4), (8, 4, 2048), (162, 8, 18), (32, 32, 1024),
+          (96, 48, 128), (24, 8, 256)]
 
 
 @pytest.mark.parametrize("prec", ["f64", "f32"])
