@@ -695,7 +695,8 @@ psolve_status build_plan(const std::vector<int> &nx, const std::vector<int> &ny,
             const char *zb = std::getenv("PSOLVE_ZBULK");
             const long long rows = (long long)g.count * g.nx * g.ny;
             g.zbulk = (dtype != PSOLVE_F64 && z_bulk_supported(g.M) && g.pz.E == 16 &&
-                       rows % z_bulk_rows(g.M) == 0 && !(zb && zb[0] == '0'))
+                       rows % z_bulk_rows(g.M, false) == 0 && rows % z_bulk_rows(g.M, true) == 0 &&
+                       !(zb && zb[0] == '0'))
                           ? 1
                           : 0;
         }
@@ -928,8 +929,9 @@ psolve_status launch_pass(const psolve_plan *p, const Group &g, int kind, const 
             zb.status = p->status;
             zb.ny = g.ny;
             zb.G = G;
-            const long long ntiles = zb.rows / z_bulk_rows(g.M);
-            const unsigned grid = (unsigned)std::min<long long>(ntiles, 2LL * p->num_sms);
+            const long long ntiles = zb.rows / z_bulk_rows(g.M, kind == 4);
+            const unsigned grid =
+                (unsigned)std::min<long long>(ntiles, (long long)z_bulk_blocks_per_sm(g.M, kind == 4) * p->num_sms);
             e = launch_z_bulk(zb, g.M, kind == 4, grid, s);
             if (e != cudaSuccess) return cuda_fail(e, kind == 0 ? "z forward pass" : "z inverse pass");
             return PSOLVE_OK;

@@ -72,15 +72,16 @@ struct ZBulkArgs {
     const float *real_in; // forward: f rows
     float *real_out;      // inverse: u rows
     float2 *spec;         // packed spectrum rows (forward output, inverse input)
-    long long rows;       // multiple of z_bulk_rows(M)
+    long long rows;       // multiple of z_bulk_rows(M, direction)
     const float2 *tw;     // e^{-2πi j/M}
     const float2 *post;   // e^{-2πi k/nz}, k < M
     int *status;
     int ny, G;            // spectrum rows in the x-split layout (spec_row; G = 1: natural)
 };
 bool z_bulk_supported(int M);
-int z_bulk_rows(int M);
-size_t z_bulk_smem(int M);
+int z_bulk_rows(int M, bool inverse);
+size_t z_bulk_smem(int M, bool inverse);
+int z_bulk_blocks_per_sm(int M, bool inverse);
 cudaError_t launch_z_bulk(const ZBulkArgs &a, int M, bool inverse, unsigned grid, cudaStream_t s);
 
 // z and y passes of a plane fused through L2 in one cluster launch.

@@ -19,13 +19,18 @@ namespace {
 
 constexpr uint64_t kZWaitNs = 2000000000ull;
 
-// M = 64, 128, 256: 16 points per thread (radix 16 × 4, 16 × 8, 16 × 16),
-// 256 threads; M = 512: 32 points per thread (radix 32 × 16: one exchange
-// instead of two), 128 threads.  All: 32 KiB tiles, two blocks per SM.
-template <int M> struct ZShape {
+// M = 64, 128, 256: 16 points per thread (radix 16 × 4, 16 × 8, 16 × 16);
+// M = 512: 32 points per thread (radix 32 × 16: one exchange instead of two).
+// Threads per block (measured on GB300 at 512³): the forward pass runs best
+// as 128-thread blocks four per SM (16 KiB tiles), the inverse as 256-thread
+// blocks two per SM (32 KiB tiles); M = 512 uses 128 threads two per SM.
+constexpr int zb_threads(int M, bool inv) { return M >= 512 ? 128 : (inv ? 256 : 128); }
+constexpr int zb_blocks(int M, bool inv) { return M >= 512 ? 2 : 512 / zb_threads(M, inv); }
+template <int M, bool INV> struct ZShape {
     static constexpr int E = M >= 512 ? 32 : 16;
     static constexpr int TL = M / E;
-    static constexpr int NT = M >= 512 ? 128 : 256;
+    static constexpr int NT = zb_threads(M, INV);
+    static constexpr int MINB = zb_blocks(M, INV);
     static constexpr int SH = E >= 32 ? 5 : 4;              // exchange padding period
     static constexpr int W = NT / TL;                       // rows per tile
     static constexpr int LP = M + (M >> 4) + 1;             // padded row pitch (complex)
@@ -33,9 +38,9 @@ template <int M> struct ZShape {
 };
 
 template <int M, bool INV>
-__global__ void __launch_bounds__(ZShape<M>::NT, 2) k_z_bulk(ZBulkArgs a)
+__global__ void __launch_bounds__(ZShape<M, INV>::NT, ZShape<M, INV>::MINB) k_z_bulk(ZBulkArgs a)
 {
-    using S = ZShape<M>;
+    using S = ZShape<M, INV>;
     constexpr int E = S::E, TL = S::TL, W = S::W;
     extern __shared__ __align__(128) unsigned char smraw[];
     float2 *buf0 = reinterpret_cast<float2 *>(smraw);
@@ -144,8 +149,8 @@ __global__ void __launch_bounds__(ZShape<M>::NT, 2) k_z_bulk(ZBulkArgs a)
 
 template <int M, bool INV> cudaError_t run(const ZBulkArgs &a, unsigned grid, cudaStream_t s)
 {
-    using S = ZShape<M>;
-    const size_t smem = z_bulk_smem(M);
+    using S = ZShape<M, INV>;
+    const size_t smem = z_bulk_smem(M, INV);
     auto kern = k_z_bulk<M, INV>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -157,11 +162,13 @@ template <int M, bool INV> cudaError_t run(const ZBulkArgs &a, unsigned grid, cu
 
 bool z_bulk_supported(int M) { return M == 64 || M == 128 || M == 256 || M == 512; }
 
-int z_bulk_rows(int M) { return M >= 512 ? 128 / (M / 32) : 256 / (M / 16); }
+int z_bulk_rows(int M, bool inverse) { return zb_threads(M, inverse) / (M / (M >= 512 ? 32 : 16)); }
 
-size_t z_bulk_smem(int M)
+int z_bulk_blocks_per_sm(int M, bool inverse) { return zb_blocks(M, inverse); }
+
+size_t z_bulk_smem(int M, bool inverse)
 {
-    const int W = z_bulk_rows(M);
+    const int W = z_bulk_rows(M, inverse);
     const int LP = M + (M >> 4) + 1;
     return (size_t)(2 * W * M + W * LP + 2 * M) * 8 + 2 * 8 + 16;
 }
