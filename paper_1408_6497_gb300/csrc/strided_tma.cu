@@ -150,6 +150,9 @@ __global__ void __launch_bounds__(TmaShape<L, CFG>::NT, TmaShape<L, CFG>::MINB)
     };
 
     long long tile = blockIdx.x;
+    // Set-up above may overlap the previous pass's last blocks; its output is
+    // read only from here on.
+    grid_dependency_wait();
     if (tid == 0 && tile < ntiles) issue(tile, buf0, &bar[0]);
 
     // exchanges in the tile buffer: rows swizzled, no spare space there
@@ -286,8 +289,15 @@ cudaError_t run(const CUtensorMap &map, const TmaArgs &a, unsigned grid, cudaStr
     auto kern = k_strided_tma<L, KIND, CFG, TC>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    kern<<<grid, S::NT, smem, s>>>(map, a);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(S::NT);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1] = {programmatic_serialization()};
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, map, a);
 }
 
 } // namespace

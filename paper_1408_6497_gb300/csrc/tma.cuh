@@ -96,6 +96,22 @@ __device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *map, u
                  : "memory");
 }
 
+// Wait until the grids this one depends on (launched with programmatic
+// stream serialisation) have completed and their writes are visible; a no-op
+// for a grid launched without that attribute.  Everything before it may
+// overlap the previous kernel's last blocks.
+__device__ __forceinline__ void grid_dependency_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+// Launch attribute that lets a kernel start while the previous kernel on the
+// stream finishes (it must call grid_dependency_wait before touching data).
+inline cudaLaunchAttribute programmatic_serialization()
+{
+    cudaLaunchAttribute at{};
+    at.id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at.val.programmaticStreamSerializationAllowed = 1;
+    return at;
+}
+
 // Contiguous bulk copy global -> shared (both 16-byte aligned, bytes % 16 == 0).
 __device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
 {

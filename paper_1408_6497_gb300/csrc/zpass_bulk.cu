@@ -71,6 +71,9 @@ __global__ void __launch_bounds__(ZShape<M, INV>::NT, ZShape<M, INV>::MINB) k_z_
         bulk_load(dst, src + tile * (long long)W * (2 * M), S::TILE_BYTES, b);
     };
     long long tile = blockIdx.x;
+    // Set-up above may overlap the previous pass's last blocks; its output is
+    // read only from here on.
+    grid_dependency_wait();
     if (tid == 0 && tile < ntiles) issue(tile, buf0, &bar[0]);
     const MapRow<S::SH> xm{w * S::LP};
 
@@ -154,8 +157,15 @@ template <int M, bool INV> cudaError_t run(const ZBulkArgs &a, unsigned grid, cu
     auto kern = k_z_bulk<M, INV>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    kern<<<grid, S::NT, smem, s>>>(a);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(S::NT);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1] = {programmatic_serialization()};
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, a);
 }
 
 } // namespace
