@@ -153,12 +153,17 @@ psolve_status psolve_error_norms(const void *a, const void *ref, size_t n, int d
 psolve_status psolve_autotune(psolve_plan *plan, void *stream);
 
 /* Per-pass timing with CUDA events recorded on the solve's own stream.
- * After psolve_set_profiling(plan, 1), every psolve_execute/psolve_adjoint
+ * After psolve_set_profiling(plan, k), k >= 1, every k-th
+ * psolve_execute/psolve_adjoint (the first, then every k-th after it)
  * records an event before the first pass and after each pass; the kernels
- * and their order are unchanged.  psolve_pass_times synchronises those
+ * and their order are unchanged.  A recorded solve runs its passes strictly
+ * one after the other (an event between two passes stops the next one from
+ * starting its set-up while the previous one drains), so k > 1 leaves most
+ * solves as fast as unprofiled ones.  psolve_pass_times synchronises the
  * events, writes into ms[i] the summed milliseconds of pass i over all
  * recorded solves (at most cap passes), sets *n_passes and *n_solves, and
- * clears the record.  psolve_set_profiling(plan, 0) stops recording. */
+ * clears the record.  psolve_set_profiling(plan, 0) stops recording; a
+ * negative k is PSOLVE_ERR_INVALID_ARG. */
 psolve_status psolve_set_profiling(psolve_plan *plan, int enable);
 psolve_status psolve_pass_times(psolve_plan *plan, double *ms, int cap, int *n_passes, int *n_solves);
 

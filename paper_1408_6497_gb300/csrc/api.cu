@@ -253,8 +253,12 @@ struct psolve_plan {
     unsigned long long wait_ns;
     unsigned long long g_wait;
     int bknob[6]; // batched launch: tile-width divisor (z, y, x) and radix order (z, y, x)
-    // per-pass profiling: one set of kPasses+1 events per recorded solve
+    // per-pass profiling: one set of kPasses+1 events per recorded solve,
+    // every prof_every-th solve
     bool profiling;
+    bool serial; // launch the passes strictly in order (host-buffer solves: no early set-up)
+    int prof_every;
+    unsigned prof_count;
     std::vector<std::vector<cudaEvent_t>> ev_used;
     std::vector<std::vector<cudaEvent_t>> ev_free;
 };
@@ -297,6 +301,7 @@ void destroy_events(psolve_plan *p)
 std::vector<cudaEvent_t> *take_events(psolve_plan *p)
 {
     if (!p->profiling) return nullptr;
+    if (p->prof_every > 1 && (p->prof_count++ % (unsigned)p->prof_every) != 0) return nullptr;
     std::vector<cudaEvent_t> set;
     if (!p->ev_free.empty()) {
         set = std::move(p->ev_free.back());
@@ -613,6 +618,9 @@ psolve_status build_plan(const std::vector<int> &nx, const std::vector<int> &ny,
     }
     p->aring = 0;
     p->profiling = false;
+    p->serial = false;
+    p->prof_every = 0;
+    p->prof_count = 0;
     p->batched = false;
     p->segs_dev = nullptr;
     p->counters = nullptr;
@@ -899,7 +907,7 @@ psolve_status run_tma_pass(const psolve_plan *p, const Group &g, T *ui, int kind
         if (kind == 2) work = std::max(work, (a.npairs + W / 2 - 1) / (W / 2));
         const int per_sm = (narrow >= 1 && narrow <= 3) ? 2 : 1;
         const unsigned grid = (unsigned)std::min<long long>(work, (long long)p->num_sms * per_sm);
-        cudaError_t e = launch_strided_tma(map, a, L, kind, narrow, grid, s);
+        cudaError_t e = launch_strided_tma(map, a, L, kind, narrow, grid, s, !p->serial);
         if (e != cudaSuccess) return cuda_fail(e, "TMA pass");
         return PSOLVE_OK;
     }
@@ -932,7 +940,7 @@ psolve_status launch_pass(const psolve_plan *p, const Group &g, int kind, const 
             const long long ntiles = zb.rows / z_bulk_rows(g.M, kind == 4);
             const unsigned grid =
                 (unsigned)std::min<long long>(ntiles, (long long)z_bulk_blocks_per_sm(g.M, kind == 4) * p->num_sms);
-            e = launch_z_bulk(zb, g.M, kind == 4, grid, s);
+            e = launch_z_bulk(zb, g.M, kind == 4, grid, s, !p->serial);
             if (e != cudaSuccess) return cuda_fail(e, kind == 0 ? "z forward pass" : "z inverse pass");
             return PSOLVE_OK;
         }
@@ -1395,7 +1403,12 @@ psolve_status host_solve(psolve_plan *plan, const void *f_host, void *u_host, vo
     }
     cudaError_t e = cudaMemcpyAsync(stage, f_host, bytes, cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return cuda_fail(e, "copy f to device");
+    // Passes of host-buffer solves run strictly in order: with early set-up
+    // their waiting blocks would hold SMs that another stream's solve of the
+    // pipeline needs (measured: 3.4 -> 6.6 ms per pipelined solve).
+    plan->serial = true;
     psolve_status st = solve(plan, stage, stage, s);
+    plan->serial = false;
     if (st != PSOLVE_OK) return st;
     e = cudaMemcpyAsync(u_host, stage, bytes, cudaMemcpyDeviceToHost, s);
     if (e != cudaSuccess) return cuda_fail(e, "copy u to host");
@@ -1601,7 +1614,10 @@ psolve_status psolve_autotune(psolve_plan *plan, void *stream)
 psolve_status psolve_set_profiling(psolve_plan *plan, int enable)
 {
     if (!plan_ok(plan)) return fail(PSOLVE_ERR_INVALID_ARG, "invalid or destroyed plan");
+    if (enable < 0) return fail(PSOLVE_ERR_INVALID_ARG, "profiling interval must be >= 0");
     plan->profiling = enable != 0;
+    plan->prof_every = enable;
+    plan->prof_count = 0;
     return PSOLVE_OK;
 }
 

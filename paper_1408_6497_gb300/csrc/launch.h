@@ -64,8 +64,10 @@ int tma_columns(int L, int cfg);
 int tma_threads(int L, int cfg);
 size_t tma_smem_bytes(int L, int cfg);
 // kind: 0 = y forward, 1 = y inverse, 2 = x with the spectral division.
+// pdl: launch with programmatic stream serialisation (the kernel's set-up
+// may overlap the previous kernel's last blocks).
 cudaError_t launch_strided_tma(const CUtensorMap &map, const TmaArgs &a, int L, int kind, int cfg,
-                               unsigned grid, cudaStream_t s);
+                               unsigned grid, cudaStream_t s, bool pdl = true);
 
 // Persistent z passes fed by 1D bulk copies (FP32, M = 256 or 512).
 struct ZBulkArgs {
@@ -82,7 +84,7 @@ bool z_bulk_supported(int M);
 int z_bulk_rows(int M, bool inverse);
 size_t z_bulk_smem(int M, bool inverse);
 int z_bulk_blocks_per_sm(int M, bool inverse);
-cudaError_t launch_z_bulk(const ZBulkArgs &a, int M, bool inverse, unsigned grid, cudaStream_t s);
+cudaError_t launch_z_bulk(const ZBulkArgs &a, int M, bool inverse, unsigned grid, cudaStream_t s, bool pdl = true);
 
 // z and y passes of a plane fused through L2 in one cluster launch.
 constexpr int kFusedThreads = 256;

@@ -282,7 +282,7 @@ __global__ void __launch_bounds__(TmaShape<L, CFG>::NT, TmaShape<L, CFG>::MINB)
 }
 
 template <int L, int KIND, int CFG, bool TC>
-cudaError_t run(const CUtensorMap &map, const TmaArgs &a, unsigned grid, cudaStream_t s)
+cudaError_t run(const CUtensorMap &map, const TmaArgs &a, unsigned grid, cudaStream_t s, bool pdl)
 {
     using S = TmaShape<L, CFG>;
     const size_t smem = tma_smem_bytes(L, S::NARROW) + (TC ? 64 + 4 * kTcFBytes : 0);
@@ -296,7 +296,7 @@ cudaError_t run(const CUtensorMap &map, const TmaArgs &a, unsigned grid, cudaStr
     cfg.stream = s;
     cudaLaunchAttribute at[1] = {programmatic_serialization()};
     cfg.attrs = at;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = pdl ? 1 : 0;
     return cudaLaunchKernelEx(&cfg, kern, map, a);
 }
 
@@ -315,31 +315,31 @@ int tma_threads(int L, int cfg) { return tma_columns(L, cfg) * L / (cfg == 2 ? 8
 bool tma_supported(int L) { return L == 256 || L == 512 || L == 1024; }
 
 cudaError_t launch_strided_tma(const CUtensorMap &map, const TmaArgs &a, int L, int kind, int cfg,
-                               unsigned grid, cudaStream_t s)
+                               unsigned grid, cudaStream_t s, bool pdl)
 {
     if (a.tc) {
         if (cfg == 2) return cudaErrorInvalidValue;
         if (cfg >= 3) { // 32 points per thread: 512-point lines only
             if (L != 512) return cudaErrorInvalidValue;
             if (cfg == 3) {
-                if (kind == 0) return run<512, 0, 3, true>(map, a, grid, s);
-                if (kind == 1) return run<512, 1, 3, true>(map, a, grid, s);
-                return run<512, 2, 3, true>(map, a, grid, s);
+                if (kind == 0) return run<512, 0, 3, true>(map, a, grid, s, pdl);
+                if (kind == 1) return run<512, 1, 3, true>(map, a, grid, s, pdl);
+                return run<512, 2, 3, true>(map, a, grid, s, pdl);
             }
-            if (kind == 0) return run<512, 0, 4, true>(map, a, grid, s);
-            if (kind == 1) return run<512, 1, 4, true>(map, a, grid, s);
-            return run<512, 2, 4, true>(map, a, grid, s);
+            if (kind == 0) return run<512, 0, 4, true>(map, a, grid, s, pdl);
+            if (kind == 1) return run<512, 1, 4, true>(map, a, grid, s, pdl);
+            return run<512, 2, 4, true>(map, a, grid, s, pdl);
         }
 #define PSOLVE_TMA_TC(LL)                                                               \
         if (L == LL) {                                                                  \
             if (cfg == 1) {                                                             \
-                if (kind == 0) return run<LL, 0, 1, true>(map, a, grid, s);             \
-                if (kind == 1) return run<LL, 1, 1, true>(map, a, grid, s);             \
-                return run<LL, 2, 1, true>(map, a, grid, s);                            \
+                if (kind == 0) return run<LL, 0, 1, true>(map, a, grid, s, pdl);             \
+                if (kind == 1) return run<LL, 1, 1, true>(map, a, grid, s, pdl);             \
+                return run<LL, 2, 1, true>(map, a, grid, s, pdl);                            \
             }                                                                           \
-            if (kind == 0) return run<LL, 0, 0, true>(map, a, grid, s);                 \
-            if (kind == 1) return run<LL, 1, 0, true>(map, a, grid, s);                 \
-            return run<LL, 2, 0, true>(map, a, grid, s);                                \
+            if (kind == 0) return run<LL, 0, 0, true>(map, a, grid, s, pdl);                 \
+            if (kind == 1) return run<LL, 1, 0, true>(map, a, grid, s, pdl);                 \
+            return run<LL, 2, 0, true>(map, a, grid, s, pdl);                                \
         }
         PSOLVE_TMA_TC(256)
         PSOLVE_TMA_TC(512)
@@ -348,9 +348,9 @@ cudaError_t launch_strided_tma(const CUtensorMap &map, const TmaArgs &a, int L, 
         return cudaErrorInvalidValue;
     }
 #define PSOLVE_TMA_KIND(LL, CF)                                                         \
-    if (kind == 0) return run<LL, 0, CF, false>(map, a, grid, s);                       \
-    if (kind == 1) return run<LL, 1, CF, false>(map, a, grid, s);                       \
-    return run<LL, 2, CF, false>(map, a, grid, s);
+    if (kind == 0) return run<LL, 0, CF, false>(map, a, grid, s, pdl);                       \
+    if (kind == 1) return run<LL, 1, CF, false>(map, a, grid, s, pdl);                       \
+    return run<LL, 2, CF, false>(map, a, grid, s, pdl);
 #define PSOLVE_TMA_CASE(LL)                                                             \
     case LL:                                                                            \
         if (cfg == 4) { PSOLVE_TMA_KIND(LL, 4) }                                        \

@@ -150,7 +150,7 @@ __global__ void __launch_bounds__(ZShape<M, INV>::NT, ZShape<M, INV>::MINB) k_z_
     }
 }
 
-template <int M, bool INV> cudaError_t run(const ZBulkArgs &a, unsigned grid, cudaStream_t s)
+template <int M, bool INV> cudaError_t run(const ZBulkArgs &a, unsigned grid, cudaStream_t s, bool pdl)
 {
     using S = ZShape<M, INV>;
     const size_t smem = z_bulk_smem(M, INV);
@@ -164,7 +164,7 @@ template <int M, bool INV> cudaError_t run(const ZBulkArgs &a, unsigned grid, cu
     cfg.stream = s;
     cudaLaunchAttribute at[1] = {programmatic_serialization()};
     cfg.attrs = at;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = pdl ? 1 : 0;
     return cudaLaunchKernelEx(&cfg, kern, a);
 }
 
@@ -183,12 +183,12 @@ size_t z_bulk_smem(int M, bool inverse)
     return (size_t)(2 * W * M + W * LP + 2 * M) * 8 + 2 * 8 + 16;
 }
 
-cudaError_t launch_z_bulk(const ZBulkArgs &a, int M, bool inverse, unsigned grid, cudaStream_t s)
+cudaError_t launch_z_bulk(const ZBulkArgs &a, int M, bool inverse, unsigned grid, cudaStream_t s, bool pdl)
 {
-    if (M == 64) return inverse ? run<64, true>(a, grid, s) : run<64, false>(a, grid, s);
-    if (M == 128) return inverse ? run<128, true>(a, grid, s) : run<128, false>(a, grid, s);
-    if (M == 256) return inverse ? run<256, true>(a, grid, s) : run<256, false>(a, grid, s);
-    if (M == 512) return inverse ? run<512, true>(a, grid, s) : run<512, false>(a, grid, s);
+    if (M == 64) return inverse ? run<64, true>(a, grid, s, pdl) : run<64, false>(a, grid, s, pdl);
+    if (M == 128) return inverse ? run<128, true>(a, grid, s, pdl) : run<128, false>(a, grid, s, pdl);
+    if (M == 256) return inverse ? run<256, true>(a, grid, s, pdl) : run<256, false>(a, grid, s, pdl);
+    if (M == 512) return inverse ? run<512, true>(a, grid, s, pdl) : run<512, false>(a, grid, s, pdl);
     return cudaErrorInvalidValue;
 }
 

@@ -155,8 +155,10 @@ class Plan:
             rc = self.lib.psolve_autotune(self.handle, _stream_handle(stream, self.device))
         _lib.check(rc, "psolve_autotune")
 
-    def set_profiling(self, enable: bool) -> None:
-        _lib.check(self.lib.psolve_set_profiling(self.handle, int(bool(enable))), "psolve_set_profiling")
+    def set_profiling(self, every) -> None:
+        """Record per-pass events on every `every`-th solve (True: every
+        solve; False or 0: stop)."""
+        _lib.check(self.lib.psolve_set_profiling(self.handle, int(every)), "psolve_set_profiling")
 
     def pass_times(self):
         """{pass name: summed ms} over the solves recorded since profiling began,

@@ -330,3 +330,20 @@ def test_argument_errors_on_device():
     # exact aliasing is allowed
     assert lib.psolve_execute(plan.handle, base, base, None) == 0
     torch.cuda.synchronize()
+
+
+def test_pass_profiling_every_kth_solve():
+    plan = Plan((64, 48, 32), dtype="f32")
+    f = torch.randn(64 * 48 * 32, device="cuda")
+    u = torch.empty_like(f)
+    plan.set_profiling(3)
+    for _ in range(7):
+        plan.execute(f, u)
+    ms, nsol = plan.pass_times()
+    assert nsol == 3  # solves 0, 3 and 6
+    assert list(ms) == ["zfwd", "yfwd", "xdiv", "yinv", "zinv"] and all(v > 0 for v in ms.values())
+    plan.set_profiling(0)
+    plan.execute(f, u)
+    assert plan.pass_times()[1] == 0
+    with pytest.raises(Exception):
+        plan.set_profiling(-1)
