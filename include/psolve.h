@@ -63,6 +63,23 @@ typedef enum {
     PSOLVE_ERR_INTERNAL = 6          /* a device-side consistency check failed                         */
 } psolve_status;
 
+/* The operator a plan inverts: the step between the forward and inverse
+ * transforms multiplies the spectrum by 1/den(k) (with the transforms' 1/N).
+ *   PSOLVE_OP_POISSON       −Δu = f (§1, Eq. 1.1; §2.1): den = 4π²|k|², 0 at
+ *                           k = 0 (the mean of f is dropped, u has mean 0).
+ *   PSOLVE_OP_HELMHOLTZ     −Δu + c·u = f, c > 0: den = 4π²|k|² + c (every
+ *                           mode kept; a constant f gives u = f/c).
+ *   PSOLVE_OP_FD_LAPLACIAN  the second-order 7-point finite-difference
+ *                           Laplacian of the grid, which the same transforms
+ *                           diagonalise (footnote to §1): den = Σ_axes
+ *                           4 n² sin²(π k/n), 0 at k = 0; u solves the
+ *                           discrete equation up to rounding. */
+typedef enum {
+    PSOLVE_OP_POISSON = 0,
+    PSOLVE_OP_HELMHOLTZ = 1,
+    PSOLVE_OP_FD_LAPLACIAN = 2
+} psolve_operator;
+
 typedef struct psolve_plan psolve_plan;
 
 /* Create a plan for `batch` equal grids nx × ny × nz (§3: the setup is paid
@@ -114,6 +131,15 @@ psolve_status psolve_execute_host(psolve_plan *plan, const void *f_host, void *u
  * until the work on `stream` completes; synchronise the streams to collect
  * u.  Calls for one plan must come from one host thread. */
 psolve_status psolve_execute_host_async(psolve_plan *plan, const void *f_host, void *u_host, void *stream);
+
+/* Choose the operator the plan's later solves (and adjoints: the operator
+ * is self-adjoint) invert; plans start with PSOLVE_OP_POISSON.  c is used by
+ * PSOLVE_OP_HELMHOLTZ only and must be positive and finite.  The first
+ * switch to PSOLVE_OP_FD_LAPLACIAN allocates the symbol tables (a few KiB,
+ * FP64).  Synchronous (blocking) and not to be called while a solve of the
+ * plan is in flight.  Returns PSOLVE_ERR_INVALID_ARG for an unknown operator
+ * or a bad c.  psolve_execute_noalloc always solves the Poisson equation. */
+psolve_status psolve_set_operator(psolve_plan *plan, int op, double c);
 
 /* Free everything the plan owns.  The plan pointer is invalid afterwards. */
 psolve_status psolve_destroy(psolve_plan *plan);

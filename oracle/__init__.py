@@ -48,6 +48,12 @@ def open_library(path: str):
                                  ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                  P(ctypes.c_double)]
     lib.oracle_solve.restype = ctypes.c_int
+    lib.oracle_solve_op.argtypes = [P(ctypes.c_double), P(ctypes.c_double), ctypes.c_int,
+                                    ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                    ctypes.c_double, P(ctypes.c_double)]
+    lib.oracle_solve_op.restype = ctypes.c_int
+    lib.oracle_op_inverse.argtypes = [ctypes.c_int, ctypes.c_double] + [ctypes.c_int] * 6
+    lib.oracle_op_inverse.restype = ctypes.c_double
     lib.oracle_dft3d.argtypes = [P(ctypes.c_double), ctypes.c_int, ctypes.c_int,
                                  ctypes.c_int, ctypes.c_int, ctypes.c_int]
     lib.oracle_dft3d.restype = None
@@ -81,14 +87,22 @@ def threads() -> int:
     return int(_load().oracle_get_threads())
 
 
-def solve(f: np.ndarray, direct: bool = False, return_imag: bool = False):
-    """u = F^{-1}[F[f] / (4π²|k|²)], û(0) = 0, in float64 (§2.1, §3)."""
+OPS = {"poisson": 0, "helmholtz": 1, "fd": 2}
+
+
+def solve(f: np.ndarray, direct: bool = False, return_imag: bool = False, op: str = "poisson",
+          c: float = 0.0):
+    """u = F^{-1}[F[f] / (4π²|k|²)], û(0) = 0, in float64 (§2.1, §3); with
+    op="helmholtz" the multiplier is 1/(4π²|k|² + c) (−Δu + c·u = f), with
+    op="fd" the inverse eigenvalues of the 7-point finite-difference
+    Laplacian."""
     f64 = np.ascontiguousarray(f, dtype=np.float64)
     if f64.ndim != 3:
         raise ValueError("f must be 3D (nx, ny, nz)")
     u = np.empty_like(f64)
     mi = ctypes.c_double(0.0)
-    rc = _load().oracle_solve(_dptr(f64), _dptr(u), *f64.shape, int(direct), ctypes.byref(mi))
+    rc = _load().oracle_solve_op(_dptr(f64), _dptr(u), *f64.shape, int(direct), OPS[op], float(c),
+                                 ctypes.byref(mi))
     if rc != 0:
         raise MemoryError("oracle_solve: allocation failed")
     return (u, mi.value) if return_imag else u

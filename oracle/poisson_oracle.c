@@ -18,6 +18,10 @@
  * û = F / (4π²|k|²) with û(0) = 0 (the mean of f is projected out), and
  *     u[x] = (1/N) sum_k û[k] e^{+2πi k·x/n}.
  *
+ * The same transforms invert two further operators (oracle_op_inverse):
+ * Helmholtz −Δu + c·u = f, multiplier 1/(4π²|k|² + c), and the 7-point
+ * finite-difference Laplacian of the grid, multiplier 1/Σ(2n²)(1 − cos 2πk/n).
+ *
  * The 1D transforms are computed either by the direct O(n^2) sum of that
  * definition, or by a plain recursive Cooley–Tukey split by the smallest factor
  * (2, then 3; anything else falls back to the direct sum) applied to full
@@ -200,10 +204,41 @@ double oracle_symbol_inverse(int jx, int jy, int jz, int nx, int ny, int nz)
     return 1.0 / (ORACLE_FOUR_PI_SQ * (double)k2);
 }
 
-/* u = F^{-1}[ F[f] / (4π²|k|²) ], û(0) = 0.  Returns 0 on success, -1 on
+/* Multiplier of the other operators the same transforms invert:
+ *   op 1, Helmholtz −Δu + c·u = f: 1/(4π²|k|² + c), c > 0, every mode kept;
+ *   op 2, the 7-point finite-difference Laplacian on the grid (h = 1/n per
+ *         axis), whose Fourier modes are eigenvectors with eigenvalue
+ *         Σ_axes (2/h²)(1 − cos(2πk/n)): 1/eigenvalue, 0 at k = 0 (the stencil
+ *         variant the paper's footnote to §1 mentions);
+ *   op 0, anything else: the Poisson multiplier above. */
+double oracle_op_inverse(int op, double c, int jx, int jy, int jz, int nx, int ny, int nz)
+{
+    long long kx = oracle_kvec(jx, nx), ky = oracle_kvec(jy, ny), kz = oracle_kvec(jz, nz);
+#if ORACLE_MUTANT == 9
+    c = 0.0 * c + 1.0; /* planted: the Helmholtz shift replaced by 1 */
+#endif
+    if (op == 1) return 1.0 / (ORACLE_FOUR_PI_SQ * (double)(kx * kx + ky * ky + kz * kz) + c);
+    if (op == 2) {
+        if (kx == 0 && ky == 0 && kz == 0) return 0.0;
+        double lam = 0.0;
+        const long long k[3] = {kx, ky, kz};
+        const int n[3] = {nx, ny, nz};
+        for (int a = 0; a < 3; ++a)
+#if ORACLE_MUTANT == 8
+            lam += 2.0 * (double)n[a] * (double)n[a] * (1.0 - creal(unit_root(2 * k[a], n[a], 1))); /* planted: 2k */
+#else
+            lam += 2.0 * (double)n[a] * (double)n[a] * (1.0 - creal(unit_root(k[a], n[a], 1)));
+#endif
+        return 1.0 / lam;
+    }
+    return oracle_symbol_inverse(jx, jy, jz, nx, ny, nz);
+}
+
+/* u = F^{-1}[ F[f] · multiplier(op) ]; op 0 gives the Poisson solve
+ * u = F^{-1}[ F[f] / (4π²|k|²) ], û(0) = 0.  Returns 0 on success, -1 on
  * allocation failure.  *max_imag receives max |Im u| before it is dropped. */
-int oracle_solve(const double *f, double *u, int nx, int ny, int nz, int direct,
-                 double *max_imag)
+int oracle_solve_op(const double *f, double *u, int nx, int ny, int nz, int direct, int op, double c,
+                    double *max_imag)
 {
     size_t N = (size_t)nx * ny * nz;
     cplx *a = (cplx *)malloc(sizeof(cplx) * N);
@@ -214,7 +249,8 @@ int oracle_solve(const double *f, double *u, int nx, int ny, int nz, int direct,
         for (int jy = 0; jy < ny; ++jy)
             for (int jz = 0; jz < nz; ++jz) {
                 size_t i = ((size_t)jx * ny + jy) * nz + jz;
-                a[i] *= oracle_symbol_inverse(jx, jy, jz, nx, ny, nz);
+                a[i] *= op == 0 ? oracle_symbol_inverse(jx, jy, jz, nx, ny, nz)
+                                : oracle_op_inverse(op, c, jx, jy, jz, nx, ny, nz);
             }
     oracle_dft3d((double *)a, nx, ny, nz, +1, direct);
     double mi = 0.0, inv_n = 1.0 / (double)N;
@@ -229,4 +265,9 @@ int oracle_solve(const double *f, double *u, int nx, int ny, int nz, int direct,
     if (max_imag) *max_imag = mi;
     free(a);
     return 0;
+}
+
+int oracle_solve(const double *f, double *u, int nx, int ny, int nz, int direct, double *max_imag)
+{
+    return oracle_solve_op(f, u, nx, ny, nz, direct, 0, 0.0, max_imag);
 }

@@ -25,6 +25,7 @@ EXPORTS = ("psolve_plan_create", "psolve_plan_create_many", "psolve_execute", "p
            "psolve_execute_host", "psolve_execute_host_async", "psolve_destroy", "psolve_instance_offset",
            "psolve_total_elements", "psolve_get_status", "psolve_debug_kvec",
            "psolve_error_norms", "psolve_autotune", "psolve_set_profiling", "psolve_pass_times", "psolve_pass_name",
+           "psolve_set_operator",
            "psolve_launches_per_solve", "psolve_debug_set_wait", "psolve_debug_tc_dft16",
            "psolve_execute_noalloc", "psolve_status_string",
            "psolve_last_error", "psolve_version")
@@ -68,6 +69,7 @@ def load(path: str | None = None):
         lib.psolve_error_norms.argtypes = [vp, vp, sz, i, ctypes.POINTER(ctypes.c_double), vp]
         lib.psolve_autotune.argtypes = [vp, vp]
         lib.psolve_set_profiling.argtypes = [vp, i]
+        lib.psolve_set_operator.argtypes = [vp, i, ctypes.c_double]
         lib.psolve_pass_times.argtypes = [vp, ctypes.POINTER(ctypes.c_double), i, ip, ip]
         lib.psolve_pass_name.argtypes = [vp, i]
         lib.psolve_pass_name.restype = ctypes.c_char_p

@@ -60,6 +60,7 @@ struct Group {
     size_t off0, stride;
     LinePlan pz, py, px;
     size_t tw_z, tw_y, tw_x, post; // complex-element offsets into the table buffer
+    size_t op_lx, op_ly, op_lz;    // offsets of the group's finite-difference symbol tables (op 2)
     int Wz, Wy, Wx;
     int cfg_y, cfg_x;    // TMA configuration of the y / x pass (-1: per-tile kernel)
     int fused;           // z and y passes fused per plane through L2: cluster size, 0 = off
@@ -227,6 +228,9 @@ struct psolve_plan {
     size_t total;
     void *tables;
     void *xsbuf; // spectrum in the x-split layout (plans that use it): the z passes go f -> xsbuf -> u
+    int op;          // spectral multiplier (OpArgs): 0 Poisson, 1 Helmholtz, 2 finite-difference Laplacian
+    double op_c;     // Helmholtz c
+    double *optab;   // finite-difference symbol tables of all groups (op 2)
     int *status;
     void *stage;
     size_t stage_bytes;
@@ -327,6 +331,7 @@ void release(psolve_plan *p)
     if (p->status) cudaFree(p->status);
     if (p->stage) cudaFree(p->stage);
     if (p->xsbuf) cudaFree(p->xsbuf);
+    if (p->optab) cudaFree(p->optab);
     for (int i = 0; i < kAsyncRing; ++i) {
         if (p->astage[i]) cudaFree(p->astage[i]);
         if (p->aev[i]) cudaEventDestroy(p->aev[i]);
@@ -490,6 +495,20 @@ void apply_tuning_cache(psolve_plan *p)
 
 // Segments of the persistent batched launch: pass-major, one per (pass,
 // instance), each with a tile width that fits kBatchThreads threads.
+// The group's spectral multiplier as the kernels read it.
+OpArgs op_args(const psolve_plan *p, const Group &g)
+{
+    OpArgs o{};
+    o.op = p->op;
+    o.c4 = p->op == 1 ? p->op_c / (4.0 * M_PI * M_PI) : 0.0;
+    if (p->op == 2 && p->optab) {
+        o.lx = p->optab + g.op_lx;
+        o.ly = p->optab + g.op_ly;
+        o.lz = p->optab + g.op_lz;
+    }
+    return o;
+}
+
 template <typename T> psolve_status setup_batched(psolve_plan *p)
 {
     using C = typename cplx_of<T>::type;
@@ -560,6 +579,7 @@ template <typename T> psolve_status setup_batched(psolve_plan *p)
                 sg.x.pl = g.px;
                 sg.x.tw = tab + g.tw_x;
                 sg.x.coef = (T)(1.0 / (4.0 * M_PI * M_PI * ((double)g.nx * g.ny * g.nz)));
+                sg.x.op = op_args(p, g);
                 sg.ntiles = sg.x.main_tiles + (sg.x.npairs + W / 2 - 1) / (W / 2);
                 smem = std::max(smem, s_smem(g.nx, W, p->dtype));
             }
@@ -610,6 +630,9 @@ psolve_status build_plan(const std::vector<int> &nx, const std::vector<int> &ny,
     p->status = nullptr;
     p->stage = nullptr;
     p->xsbuf = nullptr;
+    p->op = 0;
+    p->op_c = 0.0;
+    p->optab = nullptr;
     p->stage_bytes = 0;
     for (int i = 0; i < kAsyncRing; ++i) {
         p->astage[i] = nullptr;
@@ -898,6 +921,7 @@ psolve_status run_tma_pass(const psolve_plan *p, const Group &g, T *ui, int kind
         a.npairs = (long long)g.count * (g.ny / 2 + 1);
         a.tw = reinterpret_cast<const float2 *>(p->tables) + (kind == 2 ? g.tw_x : g.tw_y);
         a.coef = (float)(1.0 / (4.0 * M_PI * M_PI * ((double)g.nx * g.ny * g.nz)));
+        a.op = op_args(p, g);
         a.status = p->status;
         a.tc = p->dtype == PSOLVE_F32_TC ? 1 : 0;
         a.G = G;
@@ -998,6 +1022,7 @@ psolve_status launch_pass(const psolve_plan *p, const Group &g, int kind, const 
     x.pl = g.px;
     x.tw = tab + g.tw_x;
     x.coef = (T)(1.0 / (4.0 * M_PI * M_PI * ((double)g.nx * g.ny * g.nz)));
+    x.op = op_args(p, g);
     x.force_runtime = force_runtime;
     const unsigned grid = (unsigned)(x.main_tiles + (x.npairs + g.Wx / 2 - 1) / (g.Wx / 2));
     const unsigned block = (unsigned)(g.Wx * g.px.TL);
@@ -1609,6 +1634,51 @@ psolve_status psolve_autotune(psolve_plan *plan, void *stream)
     cudaError_t e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(e, "synchronise stream");
     return plan->dtype == PSOLVE_F64 ? autotune_impl<double>(plan, s) : autotune_impl<float>(plan, s);
+}
+
+psolve_status psolve_set_operator(psolve_plan *plan, int op, double c)
+{
+    if (!plan_ok(plan)) return fail(PSOLVE_ERR_INVALID_ARG, "invalid or destroyed plan");
+    if (op < PSOLVE_OP_POISSON || op > PSOLVE_OP_FD_LAPLACIAN) return fail(PSOLVE_ERR_INVALID_ARG, "unknown operator");
+    if (op == PSOLVE_OP_HELMHOLTZ && !(c > 0.0 && c < 1e300))
+        return fail(PSOLVE_ERR_INVALID_ARG, "Helmholtz c must be positive and finite");
+    DeviceGuard dg(plan->device);
+    if (dg.err != cudaSuccess) return cuda_fail(dg.err, "select device");
+    if (op == PSOLVE_OP_FD_LAPLACIAN && !plan->optab) {
+        // Λ(j) = (n/π)² sin²(π j/n) per axis and group, z indices kz = 0..M
+        std::vector<double> tab;
+        for (auto &g : plan->groups) {
+            auto add = [&](int n, int count) {
+                const size_t off = tab.size();
+                for (int j = 0; j < count; ++j) {
+                    const double s = std::sin(M_PI * (double)j / (double)n);
+                    tab.push_back((double)n * (double)n / (M_PI * M_PI) * s * s);
+                }
+                return off;
+            };
+            g.op_lx = add(g.nx, g.nx);
+            g.op_ly = add(g.ny, g.ny);
+            g.op_lz = add(g.nz, g.M + 1);
+        }
+        double *d = nullptr;
+        if (cudaMalloc(&d, tab.size() * sizeof(double)) != cudaSuccess)
+            return fail(PSOLVE_ERR_OOM, "finite-difference symbol tables: cudaMalloc failed");
+        cudaError_t e = cudaMemcpy(d, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            cudaFree(d);
+            return cuda_fail(e, "upload finite-difference symbol tables");
+        }
+        plan->optab = d;
+    }
+    plan->op = op;
+    plan->op_c = op == PSOLVE_OP_HELMHOLTZ ? c : 0.0;
+    if (plan->batched) {
+        // the persistent launch's segment table holds the multiplier
+        drop_batched(plan);
+        psolve_status st = setup_batched<float>(plan);
+        if (st != PSOLVE_OK) return st;
+    }
+    return PSOLVE_OK;
 }
 
 psolve_status psolve_set_profiling(psolve_plan *plan, int enable)

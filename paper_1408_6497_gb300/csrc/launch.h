@@ -36,6 +36,7 @@ struct TmaArgs {
     long long npairs;      // x: instances·(ny/2 + 1)
     const float2 *tw;      // e^{-2πi j/L}
     float coef;            // 1 / (4π² N)
+    OpArgs op;             // spectral multiplier (op 0: Poisson)
     int *status;           // device status word
     LinePlan pl_x;         // run-time plan of the x line (packed-column pairs)
     int tc;                // radix-16 stages on the tensor cores (cfg 0 and 1 only)

@@ -50,6 +50,28 @@ template <typename T> struct SArgs {
     int force_runtime;
 };
 
+// The solve's spectral multiplier (the step between the forward and inverse
+// transforms): û(k) = coef · F[f](k) / den(k), coef = 1/(4π²N), with
+//   op 0, Poisson −Δu = f (§2.1):      den = |k|²          (0 at k = 0: mean dropped)
+//   op 1, Helmholtz −Δu + c·u = f:     den = |k|² + c/(4π²), c > 0
+//   op 2, the second-order 7-point finite-difference Laplacian, whose
+//         eigenvalues diagonalise the same way (the stencil variant of §1):
+//         den = Λx(jx) + Λy(jy) + Λz(jz), Λ(j) = (n/π)² sin²(π j/n)
+// (den = 0 gives 0).  lx, ly, lz: device tables of Λ per index (z: kz ≤ M).
+struct OpArgs {
+    int op;
+    double c4;                  // op 1: c/(4π²)
+    const double *lx, *ly, *lz; // op 2
+};
+
+template <typename T>
+__device__ __forceinline__ T op_den(const OpArgs &o, int kx, int ky, int kz, int jx, int jy, int jz)
+{
+    if (o.op == 1) return (T)(kx * kx + ky * ky + kz * kz) + (T)o.c4;
+    if (o.op == 2) return (T)(o.lx[jx] + o.ly[jy] + o.lz[jz]);
+    return (T)(kx * kx + ky * ky + kz * kz);
+}
+
 template <typename T> struct XArgs {
     using C = typename cplx_of<T>::type;
     T *data;
@@ -61,6 +83,7 @@ template <typename T> struct XArgs {
     LinePlan pl;         // L = nx
     const C *tw;
     T coef;              // 1 / (4π² N), N = nx·ny·nz
+    OpArgs op;           // spectral multiplier (op 0: Poisson)
     int force_runtime;
 };
 
@@ -237,7 +260,8 @@ __device__ __forceinline__ void ypass_tile(const SArgs<T> &a, T *data, long long
 // G: x-split factor of the spectrum layout (1: natural; else TL % G == 0).
 template <typename T, int E, int LC, bool CG = false>
 __device__ __forceinline__ void xpair_block(T *data, int nx_rt, int ny, int M, long long sInst, long long npairs,
-                                            T coef, const LinePlan &pl, int W, int TL, long long pidx, int t,
+                                            T coef, const OpArgs &op, const LinePlan &pl, int W, int TL,
+                                            long long pidx, int t,
                                             int w, const typename cplx_of<T>::type *stw,
                                             typename cplx_of<T>::type *sx, int G = 1)
 {
@@ -282,10 +306,11 @@ __device__ __forceinline__ void xpair_block(T *data, int nx_rt, int ny, int M, l
             const C h1 = v[m];
             const C h2 = sx[jm * W + partner];
             const int kx = kvec_dev(jx, nx);
-            const int k2a = kx * kx + kys * kys;
-            const int k2b = k2a + M * M;
-            const T d0 = (k2a == 0) ? (T)0 : coef / (T)k2a;
-            const T d1 = coef / (T)k2b;
+            // symbols of the two real planes kz = 0 and kz = M
+            const T den0 = op_den<T>(op, kx, kys, 0, jx, row, 0);
+            const T den1 = op_den<T>(op, kx, kys, M, jx, row, M);
+            const T d0 = (den0 == (T)0) ? (T)0 : coef / den0;
+            const T d1 = coef / den1;
             const T sp = (d0 + d1) * (T)0.5, sm = (d0 - d1) * (T)0.5;
             v[m] = C{sp * h1.x + sm * h2.x, sp * h1.y - sm * h2.y};
         }
@@ -317,7 +342,7 @@ __device__ __forceinline__ void xfused_tile(const XArgs<T> &a, T *data, long lon
     const MapStrided map{W, w};
 
     if (tile >= a.main_tiles) {
-        xpair_block<T, E, LC, CG>(data, nx, ny, M, a.sInst, a.npairs, a.coef, a.pl, W, TL, tile - a.main_tiles,
+        xpair_block<T, E, LC, CG>(data, nx, ny, M, a.sInst, a.npairs, a.coef, a.op, a.pl, W, TL, tile - a.main_tiles,
                                   t, w, stw, sx);
         return;
     }
@@ -339,13 +364,22 @@ __device__ __forceinline__ void xfused_tile(const XArgs<T> &a, T *data, long lon
     __syncthreads();
     line_fft_any<false, LC>(v, t, a.pl, stw, sx, map, active);
     const int ky = kvec_dev(y, ny);
-    const int kyz = ky * ky + col * col;
+    if (a.op.op == 0) {
+        const int kyz = ky * ky + col * col;
 #pragma unroll
-    for (int m = 0; m < E; ++m) {
-        const int kx = kvec_dev(t + m * TL, nx);
-        const int k2 = kx * kx + kyz;
-        const T d = (k2 == 0) ? (T)0 : a.coef / (T)k2;
-        v[m] = cscale(v[m], d);
+        for (int m = 0; m < E; ++m) {
+            const int kx = kvec_dev(t + m * TL, nx);
+            const int k2 = kx * kx + kyz;
+            const T d = (k2 == 0) ? (T)0 : a.coef / (T)k2;
+            v[m] = cscale(v[m], d);
+        }
+    } else if (active) {
+#pragma unroll
+        for (int m = 0; m < E; ++m) {
+            const int jx = t + m * TL;
+            const T den = op_den<T>(a.op, kvec_dev(jx, nx), ky, col, jx, y, col);
+            v[m] = cscale(v[m], (den == (T)0) ? (T)0 : a.coef / den);
+        }
     }
     line_fft_any<true, LC>(v, t, a.pl, stw, sx, map, active);
     if (active && col != 0) {

@@ -213,14 +213,23 @@ __global__ void __launch_bounds__(TmaShape<L, CFG>::NT, TmaShape<L, CFG>::MINB)
             const int y = (int)(rest % a.ny);
             const long long inst = rest / a.ny;
             const int ky = kvec_dev(y, a.ny);
-            const int kyz = ky * ky + col * col;
+            if (a.op.op == 0) {
+                const int kyz = ky * ky + col * col;
 #pragma unroll
-            for (int m = 0; m < E; ++m) {
-                const int kx = kvec_dev(t + m * TL, L);
-                const int k2 = kx * kx + kyz;
-                // coef·(1/k²) with the hardware reciprocal: about 2 ulp in FP32
-                const float d = (k2 == 0) ? 0.f : __fdividef(a.coef, (float)k2);
-                v[m] = cscale(v[m], d);
+                for (int m = 0; m < E; ++m) {
+                    const int kx = kvec_dev(t + m * TL, L);
+                    const int k2 = kx * kx + kyz;
+                    // coef·(1/k²) with the hardware reciprocal: about 2 ulp in FP32
+                    const float d = (k2 == 0) ? 0.f : __fdividef(a.coef, (float)k2);
+                    v[m] = cscale(v[m], d);
+                }
+            } else if (active) {
+#pragma unroll
+                for (int m = 0; m < E; ++m) {
+                    const int jx = t + m * TL;
+                    const float den = op_den<float>(a.op, kvec_dev(jx, L), ky, col, jx, y, col);
+                    v[m] = cscale(v[m], den == 0.f ? 0.f : __fdividef(a.coef, den));
+                }
             }
             if constexpr (TC32) {
                 // Every warpgroup is past its forward stages (xbuf reads,
@@ -260,7 +269,7 @@ __global__ void __launch_bounds__(TmaShape<L, CFG>::NT, TmaShape<L, CFG>::MINB)
         const long long npt = (a.npairs + W / 2 - 1) / (W / 2);
         for (long long p = blockIdx.x; p < npt; p += gridDim.x) {
             xpair_block<float, E, (E == 16 || E == 32 ? L : 0)>(reinterpret_cast<float *>(a.data), L, a.ny, a.M,
-                                                                 a.sInst, a.npairs, a.coef, a.pl_x, W, TL, p, t,
+                                                                 a.sInst, a.npairs, a.coef, a.op, a.pl_x, W, TL, p, t,
                                                                  w, stw, buf0, a.G);
             __syncthreads();
         }

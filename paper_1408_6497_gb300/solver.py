@@ -37,12 +37,16 @@ def _stream_handle(stream, device) -> int:
     return int(stream)
 
 
+OPERATORS = {"poisson": 0, "helmholtz": 1, "fd": 2}
+
+
 class Plan:
     """A solve plan for `batch` grids of shape (nx, ny, nz), or for a list of
     unequal shapes (`shapes=[...]`).  Owns the device twiddle tables."""
 
     def __init__(self, shape: Sequence[int] | None = None, dtype="f32", batch: int = 1,
-                 shapes: Sequence[Sequence[int]] | None = None, device=None):
+                 shapes: Sequence[Sequence[int]] | None = None, device=None, operator="poisson",
+                 c: float = 0.0):
         self.lib = _lib.load()
         self.code = _dtype_code(dtype)
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None
@@ -65,6 +69,17 @@ class Plan:
         self.total = int(self.lib.psolve_total_elements(h))
         self.torch_dtype = _TORCH_DTYPE[self.code]
         self.np_dtype = _NP_DTYPE[self.code]
+        if operator != "poisson":
+            self.set_operator(operator, c)
+
+    def set_operator(self, operator="poisson", c: float = 0.0) -> None:
+        """The operator later solves invert: "poisson" (−Δu = f), "helmholtz"
+        (−Δu + c·u = f, c > 0) or "fd" (the 7-point finite-difference
+        Laplacian of the grid)."""
+        code = OPERATORS[operator] if isinstance(operator, str) else int(operator)
+        with torch.cuda.device(self.device):
+            rc = self.lib.psolve_set_operator(self.handle, code, float(c))
+        _lib.check(rc, "psolve_set_operator")
 
     # ----------------------------------------------------------------- utils
     def offset(self, b: int) -> int:

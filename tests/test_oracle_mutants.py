@@ -1,9 +1,10 @@
 """Planted mistakes in the oracle must each fail at least one pin (CPU only).
 
-poisson_oracle.c carries compile-time variants (ORACLE_MUTANT = 1..7) with one
+poisson_oracle.c carries compile-time variants (ORACLE_MUTANT = 1..9) with one
 plausible slip each: the 4π² factor dropped, the twiddle sign flipped, the
 wavenumber wrap-around forgotten, the x and y axes swapped in the symbol, the
-Nyquist mode dropped, the wrong normalisation, a wrong twiddle index.  Each is
+Nyquist mode dropped, the wrong normalisation, a wrong twiddle index, the
+finite-difference eigenvalue taken at 2k, the Helmholtz shift replaced.  Each is
 built into a temporary library and run through a set of the pins.
 """
 import os
@@ -15,7 +16,8 @@ import oracle
 from tests import test_oracle_pins as pins
 
 MUTANTS = {1: "4π² dropped", 2: "twiddle sign", 3: "no wrap-around", 4: "axes swapped",
-           5: "Nyquist dropped", 6: "normalisation", 7: "twiddle index"}
+           5: "Nyquist dropped", 6: "normalisation", 7: "twiddle index",
+           8: "finite-difference eigenvalue of 2k", 9: "Helmholtz shift replaced"}
 
 
 def _pin_suite(mod):
@@ -25,6 +27,8 @@ def _pin_suite(mod):
     yield lambda: pins.test_single_modes_every_octant_and_nyquist(mod, (6, 10, 4))
     yield lambda: pins.test_kvec_convention(mod, 8)
     yield lambda: pins.test_parseval_and_hermitian(mod, (12, 6, 16))
+    yield lambda: pins.test_fd_operator_solves_the_7_point_stencil(mod, (8, 6, 4))
+    yield lambda: pins.test_helmholtz_modes_and_constant(mod, 3.7)
 
 
 @pytest.mark.parametrize("mutant", sorted(MUTANTS))

@@ -235,3 +235,60 @@ def test_imaginary_part_vanishes(oracle_mod):
     f = wl.random_field((16, 12, 10), seed=5)
     _, mi = oracle_mod.solve(f, return_imag=True)
     assert mi < 1e-15
+
+
+# ------------------------------------------------- other operators (widening)
+def _neg_fd_laplacian(u):
+    """The 7-point stencil −Σ_axes (u[i+1] − 2u[i] + u[i−1]) / h², h = 1/n,
+    periodic, written out with numpy rolls (independent of any transform)."""
+    out = np.zeros_like(u)
+    for ax in range(3):
+        n = u.shape[ax]
+        out -= (np.roll(u, 1, ax) - 2.0 * u + np.roll(u, -1, ax)) * float(n * n)
+    return out
+
+
+@pytest.mark.parametrize("shape", [(8, 6, 4), (12, 16, 6), (9, 8, 10), (6, 6, 6)])
+def test_fd_operator_solves_the_7_point_stencil(oracle_mod, shape):
+    f = np.random.default_rng(sum(shape)).standard_normal(shape)
+    f -= f.mean()
+    u = oracle_mod.solve(f, op="fd")
+    r = _neg_fd_laplacian(u) - f
+    assert np.abs(r).max() <= 1e-11 * np.abs(f).max()
+    assert abs(u.mean()) <= 1e-13 * np.abs(u).max()
+
+
+def test_fd_operator_limit_is_the_spectral_one(oracle_mod):
+    # a smooth mode on a fine grid: the stencil's eigenvalue approaches 4π²|k|²
+    shape = (64, 64, 64)
+    x = np.arange(64) / 64.0
+    f = np.sin(2 * np.pi * x)[:, None, None] * np.ones(shape)
+    u_fd, u_sp = oracle_mod.solve(f, op="fd"), oracle_mod.solve(f)
+    lam = 4 * 64 ** 2 * np.sin(np.pi / 64) ** 2
+    assert np.allclose(u_fd, f / lam, rtol=0, atol=1e-13)
+    assert 0 < oracle_mod.rel_l2(u_fd, u_sp) < 1e-3  # O(h²) apart
+
+
+@pytest.mark.parametrize("c", [0.5, 3.7, 1e3])
+def test_helmholtz_modes_and_constant(oracle_mod, c):
+    shape = (8, 12, 6)
+    x = np.arange(8)[:, None, None] / 8
+    y = np.arange(12)[None, :, None] / 12
+    z = np.arange(6)[None, None, :] / 6
+    for k in [(1, 2, 0), (0, 0, 3), (2, -5, 1), (4, 6, 3)]:
+        f = np.cos(2 * np.pi * (k[0] * x + k[1] * y + k[2] * z)) + 0 * x * y * z
+        u = oracle_mod.solve(f, op="helmholtz", c=c)
+        expect = f / (4 * np.pi ** 2 * (k[0] ** 2 + k[1] ** 2 + k[2] ** 2) + c)
+        assert np.abs(u - expect).max() <= 1e-13 * np.abs(f).max()
+    u = oracle_mod.solve(np.full(shape, 2.5), op="helmholtz", c=c)
+    assert np.allclose(u, 2.5 / c, rtol=1e-14, atol=0)  # the mean is kept
+
+
+def test_operators_are_self_adjoint(oracle_mod):
+    rng = np.random.default_rng(5)
+    shape = (6, 8, 10)
+    a, b = rng.standard_normal(shape), rng.standard_normal(shape)
+    for op, c in (("helmholtz", 2.0), ("fd", 0.0)):
+        lhs = float((oracle_mod.solve(a, op=op, c=c) * b).sum())
+        rhs = float((a * oracle_mod.solve(b, op=op, c=c)).sum())
+        assert abs(lhs - rhs) <= 1e-12 * max(abs(lhs), 1.0)
