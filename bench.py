@@ -50,6 +50,10 @@ def parse():
     ap.add_argument("--precision", choices=["f32", "f32_tc"], default="f32",
                     help="f32: FP32 butterflies; f32_tc: radix-16 stages of the y/x passes on the "
                          "tensor cores (BF16 hi/lo, FP32 accumulation)")
+    ap.add_argument("--operator", choices=["poisson", "helmholtz", "fd"], default="poisson",
+                    help="operator the solve inverts: -Δu = f (default), -Δu + c·u = f, or the "
+                         "7-point finite-difference Laplacian; same passes, another multiplier")
+    ap.add_argument("--helmholtz-c", type=float, default=1.0)
     ap.add_argument("--check", action="store_true",
                     help="also report this run's rel-L2 against the FP64 oracle (a few s of CPU)")
     ap.add_argument("--no-autotune", action="store_true")
@@ -269,7 +273,7 @@ def run_ours(args):
     u_pin = torch.empty_like(f_pin).pin_memory()
     f = f_pin.to(dev)
     u = torch.empty_like(f)
-    plan = Plan(shape, dtype=args.precision, device=dev)
+    plan = Plan(shape, dtype=args.precision, device=dev, operator=args.operator, c=args.helmholtz_c)
     if not args.no_autotune:
         plan.autotune()
     stream = torch.cuda.current_stream(dev)
@@ -363,6 +367,7 @@ def run_ours(args):
         "dtype": "f32" if args.precision == "f32" else "f32+bf16x3-tc",
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "grid": list(shape), "precision": args.precision,
+                   "operator": args.operator + (f" c={args.helmholtz_c}" if args.operator == "helmholtz" else ""),
                    "l2": "inputs larger than L2 (512 MiB f and u), no flush",
                    "parallelism": "replicas" if ws > 1 else "single GPU",
                    "clock_window": "2 s soak + timed region"},
@@ -382,7 +387,8 @@ def run_ours(args):
         import oracle
         from paper_1408_6497_gb300 import workloads as wl2
         plan.execute(f, u)
-        ref = oracle.solve(wl2.sharp_source(shape).f.astype(np.float32).astype(np.float64))
+        ref = oracle.solve(wl2.sharp_source(shape).f.astype(np.float32).astype(np.float64), op=args.operator,
+                           c=args.helmholtz_c)
         line["rel_l2_vs_oracle"] = oracle.rel_l2(u.cpu().numpy().reshape(shape), ref)
     if ws == 1 and not args.no_cpu_baseline:
         rate, t, reps, cores = oracle_rate(min(n, 256), max_seconds=20.0)

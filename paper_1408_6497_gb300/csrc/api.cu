@@ -230,7 +230,8 @@ struct psolve_plan {
     void *xsbuf; // spectrum in the x-split layout (plans that use it): the z passes go f -> xsbuf -> u
     int op;          // spectral multiplier (OpArgs): 0 Poisson, 1 Helmholtz, 2 finite-difference Laplacian
     double op_c;     // Helmholtz c
-    double *optab;   // finite-difference symbol tables of all groups (op 2)
+    double *optab;   // finite-difference symbol tables of all groups (op 2): optab_n FP64, then FP32
+    size_t optab_n;
     int *status;
     void *stage;
     size_t stage_bytes;
@@ -505,6 +506,10 @@ OpArgs op_args(const psolve_plan *p, const Group &g)
         o.lx = p->optab + g.op_lx;
         o.ly = p->optab + g.op_ly;
         o.lz = p->optab + g.op_lz;
+        const float *t32 = reinterpret_cast<const float *>(p->optab + p->optab_n);
+        o.lx32 = t32 + g.op_lx;
+        o.ly32 = t32 + g.op_ly;
+        o.lz32 = t32 + g.op_lz;
     }
     return o;
 }
@@ -633,6 +638,7 @@ psolve_status build_plan(const std::vector<int> &nx, const std::vector<int> &ny,
     p->op = 0;
     p->op_c = 0.0;
     p->optab = nullptr;
+    p->optab_n = 0;
     p->stage_bytes = 0;
     for (int i = 0; i < kAsyncRing; ++i) {
         p->astage[i] = nullptr;
@@ -1660,15 +1666,22 @@ psolve_status psolve_set_operator(psolve_plan *plan, int op, double c)
             g.op_ly = add(g.ny, g.ny);
             g.op_lz = add(g.nz, g.M + 1);
         }
+        // FP64 tables, then the same rounded to FP32
+        const size_t n = tab.size();
+        std::vector<unsigned char> bytes(n * sizeof(double) + n * sizeof(float));
+        std::memcpy(bytes.data(), tab.data(), n * sizeof(double));
+        float *t32 = reinterpret_cast<float *>(bytes.data() + n * sizeof(double));
+        for (size_t i = 0; i < n; ++i) t32[i] = (float)tab[i];
         double *d = nullptr;
-        if (cudaMalloc(&d, tab.size() * sizeof(double)) != cudaSuccess)
+        if (cudaMalloc(&d, bytes.size()) != cudaSuccess)
             return fail(PSOLVE_ERR_OOM, "finite-difference symbol tables: cudaMalloc failed");
-        cudaError_t e = cudaMemcpy(d, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice);
+        cudaError_t e = cudaMemcpy(d, bytes.data(), bytes.size(), cudaMemcpyHostToDevice);
         if (e != cudaSuccess) {
             cudaFree(d);
             return cuda_fail(e, "upload finite-difference symbol tables");
         }
         plan->optab = d;
+        plan->optab_n = n;
     }
     plan->op = op;
     plan->op_c = op == PSOLVE_OP_HELMHOLTZ ? c : 0.0;

@@ -57,18 +57,26 @@ template <typename T> struct SArgs {
 //   op 2, the second-order 7-point finite-difference Laplacian, whose
 //         eigenvalues diagonalise the same way (the stencil variant of §1):
 //         den = Λx(jx) + Λy(jy) + Λz(jz), Λ(j) = (n/π)² sin²(π j/n)
-// (den = 0 gives 0).  lx, ly, lz: device tables of Λ per index (z: kz ≤ M).
+// (den = 0 gives 0).  lx, ly, lz: device tables of Λ per index (z: kz ≤ M),
+// in FP64 and rounded to FP32 (each kernel reads its own precision: the FP32
+// passes do no FP64 arithmetic).
 struct OpArgs {
     int op;
-    double c4;                  // op 1: c/(4π²)
-    const double *lx, *ly, *lz; // op 2
+    double c4;                        // op 1: c/(4π²)
+    const double *lx, *ly, *lz;       // op 2
+    const float *lx32, *ly32, *lz32;
 };
+
+template <typename T> __device__ __forceinline__ const T *op_table(const double *d, const float *f);
+template <> __device__ __forceinline__ const double *op_table<double>(const double *d, const float *) { return d; }
+template <> __device__ __forceinline__ const float *op_table<float>(const double *, const float *f) { return f; }
 
 template <typename T>
 __device__ __forceinline__ T op_den(const OpArgs &o, int kx, int ky, int kz, int jx, int jy, int jz)
 {
     if (o.op == 1) return (T)(kx * kx + ky * ky + kz * kz) + (T)o.c4;
-    if (o.op == 2) return (T)(o.lx[jx] + o.ly[jy] + o.lz[jz]);
+    if (o.op == 2)
+        return op_table<T>(o.lx, o.lx32)[jx] + op_table<T>(o.ly, o.ly32)[jy] + op_table<T>(o.lz, o.lz32)[jz];
     return (T)(kx * kx + ky * ky + kz * kz);
 }
 
@@ -373,11 +381,20 @@ __device__ __forceinline__ void xfused_tile(const XArgs<T> &a, T *data, long lon
             const T d = (k2 == 0) ? (T)0 : a.coef / (T)k2;
             v[m] = cscale(v[m], d);
         }
-    } else if (active) {
+    } else if (a.op.op == 1) {
+        const T c4 = (T)a.op.c4;
+        const int kyz = ky * ky + col * col;
 #pragma unroll
         for (int m = 0; m < E; ++m) {
-            const int jx = t + m * TL;
-            const T den = op_den<T>(a.op, kvec_dev(jx, nx), ky, col, jx, y, col);
+            const int kx = kvec_dev(t + m * TL, nx);
+            v[m] = cscale(v[m], a.coef / ((T)(kx * kx + kyz) + c4));
+        }
+    } else if (active) {
+        const T *lx = op_table<T>(a.op.lx, a.op.lx32);
+        const T lyz = op_table<T>(a.op.ly, a.op.ly32)[y] + op_table<T>(a.op.lz, a.op.lz32)[col];
+#pragma unroll
+        for (int m = 0; m < E; ++m) {
+            const T den = lx[t + m * TL] + lyz;
             v[m] = cscale(v[m], (den == (T)0) ? (T)0 : a.coef / den);
         }
     }

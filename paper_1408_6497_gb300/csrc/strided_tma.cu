@@ -223,11 +223,20 @@ __global__ void __launch_bounds__(TmaShape<L, CFG>::NT, TmaShape<L, CFG>::MINB)
                     const float d = (k2 == 0) ? 0.f : __fdividef(a.coef, (float)k2);
                     v[m] = cscale(v[m], d);
                 }
-            } else if (active) {
+            } else if (a.op.op == 1) {
+                const float c4 = (float)a.op.c4;
+                const int kyz = ky * ky + col * col;
 #pragma unroll
                 for (int m = 0; m < E; ++m) {
-                    const int jx = t + m * TL;
-                    const float den = op_den<float>(a.op, kvec_dev(jx, L), ky, col, jx, y, col);
+                    const int kx = kvec_dev(t + m * TL, L);
+                    v[m] = cscale(v[m], __fdividef(a.coef, (float)(kx * kx + kyz) + c4));
+                }
+            } else if (active) {
+                // finite-difference Laplacian: Λx per point, Λy + Λz per line
+                const float lyz = a.op.ly32[y] + a.op.lz32[col];
+#pragma unroll
+                for (int m = 0; m < E; ++m) {
+                    const float den = __ldg(&a.op.lx32[t + m * TL]) + lyz;
                     v[m] = cscale(v[m], den == 0.f ? 0.f : __fdividef(a.coef, den));
                 }
             }
