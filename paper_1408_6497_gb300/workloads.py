@@ -192,3 +192,24 @@ def random_field(shape, seed: int) -> np.ndarray:
     """White noise N(0,1) on the grid: the hardest input for a transform
     (every wavenumber excited), used for parity at small sizes."""
     return np.random.default_rng(seed).standard_normal(tuple(shape))
+
+
+def sphere_layer(shape, alpha: float, R: float = 0.25, centre: float = 0.5):
+    """The paper's second time-to-solution case (§3, Tables 8-9): the exact
+    solution u = exp(-(r/R)^α), r the (minimum-image) distance to the cube's
+    centre, a sharp layer at r = R, and its source f = -Δu in closed form:
+    with s = (r/R)^α,  -Δu = (α s u / r²)(α + 1 - α s)  (radial Laplacian
+    u'' + 2u'/r).  For α >= 10 and R = 1/4, u and f vanish at the cube's faces
+    to far below double precision, so both are smooth periodic fields.
+    Returns (f, u) in float64."""
+    axes = []
+    for n in shape:
+        d = np.arange(n) / n - centre
+        d -= np.round(d)  # minimum image
+        axes.append(d)
+    r2 = axes[0][:, None, None] ** 2 + axes[1][None, :, None] ** 2 + axes[2][None, None, :] ** 2
+    s = (r2 / (R * R)) ** (alpha / 2.0)
+    u = np.exp(-s)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        f = np.where(r2 > 0, alpha * s * u / r2 * (alpha + 1.0 - alpha * s), 0.0)
+    return f, u

@@ -94,3 +94,15 @@ def test_operator_argument_errors(op, c):
     plan = Plan((8, 8, 8), dtype="f32")
     with pytest.raises(Exception):
         plan.set_operator(op, c)
+
+
+def test_sphere_layer_case_on_gpu_matches_oracle():
+    """The sharp-layer case of the resolution study, FP64 on the GPU, has the
+    oracle's error at the same grid."""
+    from paper_1408_6497_gb300 import study
+    for n in (32, 64):
+        r = study.solve_case(n, 10.0, "f64")
+        f, u = wl.sphere_layer((n, n, n), 10.0)
+        ue = u - u.mean()
+        e_or = np.abs(oracle.solve(f) - ue).max() / np.abs(ue).max()
+        assert abs(r["rel_linf"] - e_or) <= 1e-9 * max(e_or, 1.0), (n, r, e_or)
