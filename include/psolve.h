@@ -138,7 +138,13 @@ psolve_status psolve_execute_host_async(psolve_plan *plan, const void *f_host, v
  * switch to PSOLVE_OP_FD_LAPLACIAN allocates the symbol tables (a few KiB,
  * FP64).  Synchronous (blocking) and not to be called while a solve of the
  * plan is in flight.  Returns PSOLVE_ERR_INVALID_ARG for an unknown operator
- * or a bad c.  psolve_execute_noalloc always solves the Poisson equation. */
+ * or a bad c.  With an operator other than Poisson, FP32 grids whose x
+ * lines have 256, 512 or 1024 points keep the TMA-fed x pass (forward x
+ * transform, multiplier, inverse x transform) at its default configuration;
+ * every other case runs it in the per-tile kernels, in FP32 also for
+ * PSOLVE_F32_TC plans (psolve_pass_name then reports "xdiv").  Grids keep
+ * the natural spectrum layout.
+ * psolve_execute_noalloc always solves the Poisson equation. */
 psolve_status psolve_set_operator(psolve_plan *plan, int op, double c);
 
 /* Free everything the plan owns.  The plan pointer is invalid afterwards. */

@@ -881,7 +881,9 @@ bool encode_map4(CUtensorMap *m, void *base, const uint64_t (&d)[4], const uint3
 // device, and G divides nx and the x line's threads.
 int xs_factor(const psolve_plan *p, const Group &g, bool host_io)
 {
-    if (!p->xsbuf || g.xs <= 1 || host_io || g.fused > 0 || !g.zbulk || g.cfg_y < 0 || g.cfg_x < 0) return 1;
+    if (!p->xsbuf || g.xs <= 1 || host_io || g.fused > 0 || !g.zbulk || g.cfg_y < 0 || g.cfg_x < 0 ||
+        p->op != PSOLVE_OP_POISSON)
+        return 1;
     if (g.nx % g.xs != 0 || tma_threads(g.nx, g.cfg_x) / tma_columns(g.nx, g.cfg_x) % g.xs != 0) return 1;
     if ((g.nx < 256 ? g.nx : 256) % g.xs != 0) return 1;
     return g.xs;
@@ -1013,7 +1015,11 @@ psolve_status launch_pass(const psolve_plan *p, const Group &g, int kind, const 
         if (e != cudaSuccess) return cuda_fail(e, kind == 1 ? "y forward pass" : "y inverse pass");
         return PSOLVE_OK;
     }
-    if (g.cfg_x >= 0) return run_tma_pass<T>(p, g, ui, 2, s, G);
+    // Other operators than Poisson have TMA x-pass instantiations for the
+    // default FP32 configurations only; otherwise they take the per-tile pass.
+    if (g.cfg_x >= 0 && (p->op == PSOLVE_OP_POISSON ||
+                         (p->dtype == PSOLVE_F32 && tma_ops_supported(g.nx, g.cfg_x))))
+        return run_tma_pass<T>(p, g, ui, 2, s, G);
     XArgs<T> x{};
     x.data = ui;
     x.batch = g.count;
@@ -1746,7 +1752,7 @@ const char *psolve_pass_name(const psolve_plan *plan, int i)
     if (plan->dtype == PSOLVE_F32_TC) {
         const Group &g = plan->groups[0];
         if ((i == 1 || i == 3) && g.cfg_y >= 0) return i == 1 ? "yfwd_tc" : "yinv_tc";
-        if (i == 2 && g.cfg_x >= 0) return "xdiv_tc";
+        if (i == 2 && g.cfg_x >= 0 && plan->op == PSOLVE_OP_POISSON) return "xdiv_tc";
     }
     return kPassNames[i];
 }

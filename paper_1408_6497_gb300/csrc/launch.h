@@ -36,7 +36,7 @@ struct TmaArgs {
     long long npairs;      // x: instances·(ny/2 + 1)
     const float2 *tw;      // e^{-2πi j/L}
     float coef;            // 1 / (4π² N)
-    OpArgs op;             // spectral multiplier (op 0: Poisson)
+    OpArgs op;             // spectral multiplier (op 0: Poisson; others: tma_ops_supported configurations)
     int *status;           // device status word
     LinePlan pl_x;         // run-time plan of the x line (packed-column pairs)
     int tc;                // radix-16 stages on the tensor cores (cfg 0 and 1 only)
@@ -56,6 +56,7 @@ __host__ __device__ inline long long spec_row(long long x, long long y, int ny, 
     return ((x / G) * ny + y) * G + (x % G);
 }
 bool tma_supported(int L);
+bool tma_ops_supported(int L, int cfg);
 // cfg 0: 64 KiB tiles, 16 points per thread, one 512-thread block per SM;
 // cfg 1: 32 KiB tiles, 16 points per thread, 256-thread blocks, two per SM;
 // cfg 2: 32 KiB tiles, 8 points per thread, 512-thread blocks, two per SM;

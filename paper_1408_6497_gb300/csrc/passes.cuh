@@ -266,7 +266,8 @@ __device__ __forceinline__ void ypass_tile(const SArgs<T> &a, T *data, long long
 // `pidx` takes pairs pidx·(W/2) .. pidx·(W/2) + W/2 - 1.  All threads of the
 // block must call it (it synchronises).
 // G: x-split factor of the spectrum layout (1: natural; else TL % G == 0).
-template <typename T, int E, int LC, bool CG = false>
+// OPS = false: the Poisson multiplier only (op is not read).
+template <typename T, int E, int LC, bool CG = false, bool OPS = true>
 __device__ __forceinline__ void xpair_block(T *data, int nx_rt, int ny, int M, long long sInst, long long npairs,
                                             T coef, const OpArgs &op, const LinePlan &pl, int W, int TL,
                                             long long pidx, int t,
@@ -315,8 +316,14 @@ __device__ __forceinline__ void xpair_block(T *data, int nx_rt, int ny, int M, l
             const C h2 = sx[jm * W + partner];
             const int kx = kvec_dev(jx, nx);
             // symbols of the two real planes kz = 0 and kz = M
-            const T den0 = op_den<T>(op, kx, kys, 0, jx, row, 0);
-            const T den1 = op_den<T>(op, kx, kys, M, jx, row, M);
+            T den0, den1;
+            if constexpr (OPS) {
+                den0 = op_den<T>(op, kx, kys, 0, jx, row, 0);
+                den1 = op_den<T>(op, kx, kys, M, jx, row, M);
+            } else {
+                den0 = (T)(kx * kx + kys * kys);
+                den1 = (T)(kx * kx + kys * kys + M * M);
+            }
             const T d0 = (den0 == (T)0) ? (T)0 : coef / den0;
             const T d1 = coef / den1;
             const T sp = (d0 + d1) * (T)0.5, sm = (d0 - d1) * (T)0.5;

@@ -51,7 +51,7 @@ template <int L, int CFG> struct TmaShape {
 // thread (512 = 32 × 16) the radix-32 stage stays in FP32 and the radix-16
 // stage, the last, runs on the tensor cores per warpgroup (tc32_last_stage),
 // its operand rows in the tile buffer once the tile has been read.
-template <int L, int KIND, int CFG, bool TC>
+template <int L, int KIND, int CFG, bool TC, bool OPS = false>
 __global__ void __launch_bounds__(TmaShape<L, CFG>::NT, TmaShape<L, CFG>::MINB)
     k_strided_tma(const __grid_constant__ CUtensorMap tmap, TmaArgs a)
 {
@@ -213,7 +213,9 @@ __global__ void __launch_bounds__(TmaShape<L, CFG>::NT, TmaShape<L, CFG>::MINB)
             const int y = (int)(rest % a.ny);
             const long long inst = rest / a.ny;
             const int ky = kvec_dev(y, a.ny);
-            if (a.op.op == 0) {
+            if constexpr (!OPS) {
+                // the Poisson multiplier (the instantiation for other
+                // operators is separate, so this one keeps its registers)
                 const int kyz = ky * ky + col * col;
 #pragma unroll
                 for (int m = 0; m < E; ++m) {
@@ -277,9 +279,9 @@ __global__ void __launch_bounds__(TmaShape<L, CFG>::NT, TmaShape<L, CFG>::MINB)
         // Packed column pairs, one group of W/2 pairs per block-iteration.
         const long long npt = (a.npairs + W / 2 - 1) / (W / 2);
         for (long long p = blockIdx.x; p < npt; p += gridDim.x) {
-            xpair_block<float, E, (E == 16 || E == 32 ? L : 0)>(reinterpret_cast<float *>(a.data), L, a.ny, a.M,
-                                                                 a.sInst, a.npairs, a.coef, a.op, a.pl_x, W, TL, p, t,
-                                                                 w, stw, buf0, a.G);
+            xpair_block<float, E, (E == 16 || E == 32 ? L : 0), false, OPS>(
+                reinterpret_cast<float *>(a.data), L, a.ny, a.M, a.sInst, a.npairs, a.coef, a.op, a.pl_x, W,
+                TL, p, t, w, stw, buf0, a.G);
             __syncthreads();
         }
     }
@@ -299,12 +301,12 @@ __global__ void __launch_bounds__(TmaShape<L, CFG>::NT, TmaShape<L, CFG>::MINB)
     }
 }
 
-template <int L, int KIND, int CFG, bool TC>
+template <int L, int KIND, int CFG, bool TC, bool OPS = false>
 cudaError_t run(const CUtensorMap &map, const TmaArgs &a, unsigned grid, cudaStream_t s, bool pdl)
 {
     using S = TmaShape<L, CFG>;
     const size_t smem = tma_smem_bytes(L, S::NARROW) + (TC ? 64 + 4 * kTcFBytes : 0);
-    auto kern = k_strided_tma<L, KIND, CFG, TC>;
+    auto kern = k_strided_tma<L, KIND, CFG, TC, OPS>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg{};
@@ -332,9 +334,21 @@ int tma_threads(int L, int cfg) { return tma_columns(L, cfg) * L / (cfg == 2 ? 8
 
 bool tma_supported(int L) { return L == 256 || L == 512 || L == 1024; }
 
+// TMA x-pass configurations instantiated for every operator.
+bool tma_ops_supported(int L, int cfg) { return (L == 512 && cfg == 3) || (L == 1024 && cfg == 4) || (L == 256 && cfg == 1); }
+
 cudaError_t launch_strided_tma(const CUtensorMap &map, const TmaArgs &a, int L, int kind, int cfg,
                                unsigned grid, cudaStream_t s, bool pdl)
 {
+    if (kind == 2 && a.op.op != 0) {
+        // other operators: the default FP32 configurations only (y passes
+        // carry no multiplier and ignore a.op)
+        if (a.tc) return cudaErrorInvalidValue;
+        if (L == 512 && cfg == 3) return run<512, 2, 3, false, true>(map, a, grid, s, pdl);
+        if (L == 1024 && cfg == 4) return run<1024, 2, 4, false, true>(map, a, grid, s, pdl);
+        if (L == 256 && cfg == 1) return run<256, 2, 1, false, true>(map, a, grid, s, pdl);
+        return cudaErrorInvalidValue;
+    }
     if (a.tc) {
         if (cfg == 2) return cudaErrorInvalidValue;
         if (cfg >= 3) { // 32 points per thread: 512-point lines only
