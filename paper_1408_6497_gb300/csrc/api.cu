@@ -11,6 +11,7 @@
 #include <cstdint>
 #include <cstdio>
 #include <cstdlib>
+#include <cstddef>
 #include <cstring>
 #include <map>
 #include <memory>
@@ -530,6 +531,13 @@ template <typename T> psolve_status setup_batched(psolve_plan *p)
         make_line_plan(g.ny, g.py, p->bknob[4], 2);
         make_line_plan(g.nx, g.px, p->bknob[5], 2);
     }
+    // Radix order 0 with a compile-time plan for the line: the kernel's
+    // instantiation for that length (same stages, constants folded).
+    const char *cte = std::getenv("PSOLVE_BATCH_CT");
+    const bool use_ct = !(cte && cte[0] == '0');
+    auto lc_of = [&](const LinePlan &pl, int order) {
+        return (use_ct && order == 0 && batched_ct_supported(pl.L, pl.E)) ? pl.L : 0;
+    };
     for (int pass = 0; pass < 5; ++pass) {
         for (int i = 0; i < B; ++i) {
             const Group &g = p->groups[i];
@@ -544,6 +552,7 @@ template <typename T> psolve_status setup_batched(psolve_plan *p)
                 const int LP = M + (M >> 4) + 1;
                 while (W > 1 && (size_t)(M + (size_t)W * LP) * cs > kSmemCap) W /= 2;
                 sg.E = g.pz.E;
+                sg.lc = lc_of(g.pz, p->bknob[3]);
                 sg.z.rows = (long long)g.nx * g.ny;
                 sg.z.nz = g.nz;
                 sg.z.M = M;
@@ -557,6 +566,7 @@ template <typename T> psolve_status setup_batched(psolve_plan *p)
                 int W = std::min(M, std::max(1, NT / g.py.TL / p->bknob[1]));
                 while (W > 1 && s_smem(g.ny, W, p->dtype) > kSmemCap) W /= 2;
                 sg.E = g.py.E;
+                sg.lc = lc_of(g.py, p->bknob[4]);
                 sg.y.nplanes = g.nx;
                 sg.y.sPlane = (long long)g.ny * M;
                 sg.y.sL = M;
@@ -572,6 +582,7 @@ template <typename T> psolve_status setup_batched(psolve_plan *p)
                 while (W > 2 && s_smem(g.nx, W, p->dtype) > kSmemCap) W /= 2;
                 if (W * g.px.TL > NT) return fail(PSOLVE_ERR_UNSUPPORTED_SIZE, "x line too long for a batch tile");
                 sg.E = g.px.E;
+                sg.lc = lc_of(g.px, p->bknob[5]);
                 sg.x.batch = 1;
                 sg.x.nx = g.nx;
                 sg.x.ny = g.ny;
@@ -1776,10 +1787,13 @@ psolve_status psolve_debug_set_wait(psolve_plan *plan, unsigned long long wait_n
     unsigned char entry[4096];
     if (seg_bytes > sizeof(entry)) return fail(PSOLVE_ERR_INTERNAL, "segment too large");
     std::memcpy(entry, plan->segs_host.data() + (size_t)target * seg_bytes, seg_bytes);
+    // the leading int fields have the same offsets in BatchSeg<float> and <double>
+    const size_t off_need = offsetof(BatchSeg<float>, need);
+    static_assert(offsetof(BatchSeg<float>, need) == offsetof(BatchSeg<double>, need), "segment layout");
     int need = 0;
-    std::memcpy(&need, entry + 3 * sizeof(int), sizeof(int));
+    std::memcpy(&need, entry + off_need, sizeof(int));
     if (unsatisfiable) ++need;
-    std::memcpy(entry + 3 * sizeof(int), &need, sizeof(int));
+    std::memcpy(entry + off_need, &need, sizeof(int));
     cudaError_t e = cudaMemcpy((char *)plan->segs_dev + (size_t)target * seg_bytes, entry, seg_bytes,
                                cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cuda_fail(e, "update segment");

@@ -44,21 +44,58 @@ __device__ bool wait_count(const int *counter, long long need, unsigned long lon
     }
 }
 
-template <typename T, int E> __device__ __forceinline__ void run_item(const BatchSeg<T> &sg, long long tile,
-                                                                    const T *f, T *u, unsigned char *smem)
+// One tile of one pass; LC > 0: the line length, with its compile-time plan.
+// Not inlined: each variant gets its own register allocation (a tile is
+// thousands of instructions, so the call costs nothing measurable).
+template <typename T, int E, int LC> __device__ __noinline__ void run_item(const BatchSeg<T> *__restrict__ sgp,
+                                                                          long long tile, const T *f, T *u,
+                                                                          unsigned char *smem)
 {
+    const BatchSeg<T> &sg = *sgp;
     T *ui = u + sg.off;
     switch (sg.kind) {
-    case 0: zfwd_tile<T, E, 0, true>(sg.z, f + sg.off, ui, tile, smem); break;
-    case 1: ypass_tile<T, E, false, 0, true>(sg.y, ui, tile, smem); break;
-    case 2: xfused_tile<T, E, 0, true>(sg.x, ui, tile, smem); break;
-    case 3: ypass_tile<T, E, true, 0, true>(sg.y, ui, tile, smem); break;
-    default: zinv_tile<T, E, 0, true>(sg.z, ui, ui, tile, smem); break;
+    case 0: zfwd_tile<T, E, LC, true>(sg.z, f + sg.off, ui, tile, smem); break;
+    case 1: ypass_tile<T, E, false, LC, true>(sg.y, ui, tile, smem); break;
+    case 2: xfused_tile<T, E, LC, true>(sg.x, ui, tile, smem); break;
+    case 3: ypass_tile<T, E, true, LC, true>(sg.y, ui, tile, smem); break;
+    default: zinv_tile<T, E, LC, true>(sg.z, ui, ui, tile, smem); break;
+    }
+}
+
+// Compile-time plans: 2^a-point lines with 16 points per thread, 3·2^a-point
+// lines with 12 (the run-time planner's choices for batches).
+template <typename T> __device__ __forceinline__ void run_item_any(const BatchSeg<T> &sg, long long tile,
+                                                                   const T *f, T *u, unsigned char *smem)
+{
+    switch (sg.E) {
+    case 4: run_item<T, 4, 0>(&sg, tile, f, u, smem); break;
+    case 8: run_item<T, 8, 0>(&sg, tile, f, u, smem); break;
+    case 12:
+        switch (sg.lc) {
+        case 12: run_item<T, 12, 12>(&sg, tile, f, u, smem); break;
+        case 24: run_item<T, 12, 24>(&sg, tile, f, u, smem); break;
+        case 48: run_item<T, 12, 48>(&sg, tile, f, u, smem); break;
+        case 96: run_item<T, 12, 96>(&sg, tile, f, u, smem); break;
+        case 192: run_item<T, 12, 192>(&sg, tile, f, u, smem); break;
+        default: run_item<T, 12, 0>(&sg, tile, f, u, smem); break;
+        }
+        break;
+    case 16:
+        switch (sg.lc) {
+        case 16: run_item<T, 16, 16>(&sg, tile, f, u, smem); break;
+        case 32: run_item<T, 16, 32>(&sg, tile, f, u, smem); break;
+        case 64: run_item<T, 16, 64>(&sg, tile, f, u, smem); break;
+        case 128: run_item<T, 16, 128>(&sg, tile, f, u, smem); break;
+        case 256: run_item<T, 16, 256>(&sg, tile, f, u, smem); break;
+        default: run_item<T, 16, 0>(&sg, tile, f, u, smem); break;
+        }
+        break;
+    default: break;
     }
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kBatchThreads, PSOLVE_BATCH_MINB) k_batched(const BatchSeg<T> *__restrict__ segs, int nseg,
+__global__ void __launch_bounds__(kBatchThreads, PSOLVE_BATCH_MINB) k_batched(const BatchSeg<T> *segs, int nseg,
                                                               long long total, const T *f, T *u,
                                                               unsigned long long *work, int *done, int *status,
                                                               unsigned long long wait_ns)
@@ -94,13 +131,7 @@ __global__ void __launch_bounds__(kBatchThreads, PSOLVE_BATCH_MINB) k_batched(co
         if (item >= total || s_abort) return;
         const BatchSeg<T> &sg = segs[s_seg];
         const long long tile = item - sg.first;
-        switch (sg.E) {
-        case 4: run_item<T, 4>(sg, tile, f, u, smraw); break;
-        case 8: run_item<T, 8>(sg, tile, f, u, smraw); break;
-        case 12: run_item<T, 12>(sg, tile, f, u, smraw); break;
-        case 16: run_item<T, 16>(sg, tile, f, u, smraw); break;
-        default: break;
-        }
+        run_item_any<T>(sg, tile, f, u, smraw);
         // Publish this tile: the barrier orders every thread's stores before
         // thread 0's fence (cumulative at GPU scope), then one count.
         __syncthreads();
@@ -124,5 +155,12 @@ template <typename T> cudaError_t batched_prepare(size_t smem)
 template cudaError_t batched_prepare<float>(size_t);
 
 bool batched_supports_E(int E) { return E == 4 || E == 8 || E == 12 || E == 16; }
+
+bool batched_ct_supported(int L, int E)
+{
+    if (E == 12) return L == 12 || L == 24 || L == 48 || L == 96 || L == 192;
+    if (E == 16) return L == 16 || L == 32 || L == 64 || L == 128 || L == 256;
+    return false;
+}
 
 } // namespace psolve

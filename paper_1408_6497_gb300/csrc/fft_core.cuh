@@ -524,7 +524,8 @@ __device__ __forceinline__ void line_fft_any(C (&v)[E], int t, const LinePlan &p
                                              C *sm, const Map &map, bool active)
 {
     if constexpr (LC > 0) {
-        static_assert(ct_E(LC) == E || E == 32, "compile-time plan needs its own points per thread");
+        static_assert(LC % E == 0 && (ct_pow3(LC) == 0 || E % 3 == 0),
+                      "compile-time plan: E divides the line, and holds the radix-3 factor if there is one");
         line_fft_ct_from<INV, LC, 0>(v, t, tw, sm, map, active);
     } else {
         line_fft<INV>(v, t, pl, tw, sm, map, active);

@@ -111,6 +111,7 @@ constexpr int kBatchThreads = PSOLVE_BATCH_THREADS;
 template <typename T> struct BatchSeg {
     int kind;           // 0 zfwd, 1 yfwd, 2 xdiv, 3 yinv, 4 zinv
     int E;              // points per thread of the pass's line
+    int lc;             // line length of a compile-time plan (batched_ct_supported), else 0
     int dep;            // segment that must complete first, or -1
     int need;           // completed tiles of `dep` to wait for (its tile count)
     long long first;    // first item number of this segment
@@ -123,6 +124,9 @@ template <typename T> struct BatchSeg {
 template <typename T> const void *batched_kernel();
 template <typename T> cudaError_t batched_prepare(size_t smem);
 bool batched_supports_E(int E);
+// (line length, points per thread) pairs the batched kernel holds compile-time
+// plans for (radix-3 stages first, then the largest power-of-two radices).
+bool batched_ct_supported(int L, int E);
 
 // Twiddles e^{-2πi j/denom}, j < count, computed in FP64 and rounded to T.
 template <typename T>
