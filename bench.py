@@ -157,11 +157,20 @@ def gpu_uuid(torch, dev):
         return None
 
 
+# Sources of the kernels whose DRAM traffic profiles/ncu_traffic.json records
+# (the z bulk and TMA y/x passes): their translation units, every header they
+# include, and the host code that picks their configurations and grids.
+TRAFFIC_SOURCES = ("paper_1408_6497_gb300/csrc/strided_tma.cu", "paper_1408_6497_gb300/csrc/zpass_bulk.cu",
+                   "paper_1408_6497_gb300/csrc/launch.h", "paper_1408_6497_gb300/csrc/passes.cuh",
+                   "paper_1408_6497_gb300/csrc/fft_core.cuh", "paper_1408_6497_gb300/csrc/tc.cuh",
+                   "paper_1408_6497_gb300/csrc/tma.cuh", "paper_1408_6497_gb300/csrc/api.cu",
+                   "include/psolve.h")
+
+
 def kernel_digest() -> str:
     h = hashlib.sha256()
-    csrc = os.path.join(ROOT, "paper_1408_6497_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        with open(os.path.join(csrc, f), "rb") as fh:
+    for f in TRAFFIC_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
             h.update(f.encode())
             h.update(fh.read())
     return h.hexdigest()[:16]

@@ -12,7 +12,10 @@
 // Data written by other blocks of the same launch are read with L2-only
 // loads (ld.global.cg).  Lines are planned with at most 16 points per
 // thread (12 for lengths 3·2^a); lines needing 2, 3 or 6 are not covered
-// (the planner then launches per pass).
+// (the planner then launches per pass).  Lines of 12…256 points in radix
+// order 0 run compile-time plans (batched_ct_supported), the others run-time
+// plans; each (points per thread, length) variant is a separate device
+// function, so the one kernel does not carry the registers of the largest.
 #include "psolve.h"
 #include "launch.h"
 #include "tma.cuh"
