@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--check", action="store_true",
                     help="also report this run's rel-L2 against the FP64 oracle (a few s of CPU)")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--oracle-threads", type=int, default=0,
+                    help="--impl reference: OpenMP threads of the FP64 oracle (0: all host cores)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
 
@@ -220,6 +222,9 @@ def run_reference(args):
     import oracle
     from paper_1408_6497_gb300 import workloads as wl
     oracle.build()
+    oracle.set_threads(args.oracle_threads)
+    if args.workload == "batch64":
+        return run_reference_batch(args, oracle, wl, ws, rank)
     # Size each step so that warmup + steps fit in about two minutes.
     probe_t = None
     grid = 64
@@ -251,6 +256,45 @@ def run_reference(args):
                        "grid": [grid] * 3, "precision": "f64", "device": "host cores"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
                              "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    emit(line, rank)
+    return 0
+
+
+def run_reference_batch(args, oracle, wl, ws, rank):
+    """The oracle on the 64-grid batch: each step solves the first m grids,
+    m as large as lets warmup + steps end within about two minutes."""
+    shapes = wl.batch_shapes(64)
+    fs = [wl.batch_instance(s, b).f for b, s in enumerate(shapes)]
+    t0 = time.perf_counter()
+    oracle.solve(fs[0])
+    per_unknown = (time.perf_counter() - t0) / fs[0].size
+    budget = 120.0 / max(1, args.steps + args.warmup)
+    m, n = 0, 0
+    while m < len(fs) and (m == 0 or (n + fs[m].size) * per_unknown <= budget):
+        n += fs[m].size
+        m += 1
+    sample = fs[:m]
+    for _ in range(args.warmup):
+        for f in sample:
+            oracle.solve(f)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for f in sample:
+            oracle.solve(f)
+    el = time.perf_counter() - t0
+    value = n / (el / args.steps)
+    desc = (f"{args.steps} FP64 oracle solve(s) of the first {m} of the 64 uneven grids "
+            f"({n} unknowns per step)")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "batch64: 64 uneven grids, axes from {24, ..., 256}, 16 Gaussians each"
+                                   + ("" if m == len(fs) else f" (first {m} grids)"),
+                       "grids": m, "precision": "f64", "device": "host cores"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+                             "sample": desc},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     emit(line, rank)
     return 0
