@@ -67,3 +67,21 @@ def test_reference_arm_other_ranks_exit_without_work():
                        timeout=120)
     assert r.returncode == 0
     assert r.stdout.strip() == ""
+
+
+def test_l2_note_flags_grids_whose_spectrum_fits_in_l2():
+    b = _bench()
+    # 512^3: half spectrum 512·512·257·8 B = 539 MB > 129 MB
+    assert b.l2_note((512, 512, 512)).startswith("every pass's arrays larger")
+    # 256^3: 67 MB spectrum stays in L2 between passes
+    assert b.l2_note((256, 256, 256)).startswith("L2-influenced")
+
+
+def test_traffic_record_matches_current_sources_or_is_dropped(monkeypatch):
+    b = _bench()
+    # the committed record is keyed to the sources of the recorded kernels
+    rec = b.recorded_traffic("xdiv", 512 ** 3)
+    assert rec is None or 1.0e9 < rec < 1.2e9  # 8 B per unknown = 1.07 GB per pass
+    # a record keyed to other sources is not used
+    monkeypatch.setattr(b, "kernel_digest", lambda: "0000000000000000")
+    assert b.recorded_traffic("xdiv", 512 ** 3) is None
