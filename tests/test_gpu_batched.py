@@ -53,6 +53,27 @@ def test_batch64_each_instance_matches_oracle():
     print(f"batch of 64: {total} unknowns, worst rel-L2 {worst:.2e}")
 
 
+def test_compile_time_and_run_time_plans_agree(monkeypatch):
+    # every axis length of the batch draw: lines of 12…256 points run
+    # compile-time plans by default, run-time plans with PSOLVE_BATCH_CT=0
+    shapes = [(24, 32, 48), (64, 96, 128), (192, 256, 24), (48, 24, 192), (256, 64, 32)]
+    plan = Plan(dtype="f32", shapes=shapes)
+    flat, fs = fill(plan, shapes, seed_offset=50)
+    u_ct = plan.execute(flat)
+    plan.status()
+    monkeypatch.setenv("PSOLVE_BATCH_CT", "0")
+    plan_rt = Plan(dtype="f32", shapes=shapes)
+    assert plan_rt.launches_per_solve == 1
+    u_rt = plan_rt.execute(flat)
+    plan_rt.status()
+    for b, s in enumerate(shapes):
+        ref = oracle.solve(fs[b].astype(np.float64))
+        a, r = plan.view(u_ct, b).cpu().numpy(), plan_rt.view(u_rt, b).cpu().numpy()
+        assert oracle.rel_l2(a, ref) <= 5e-6, (s, "compile-time")
+        assert oracle.rel_l2(r, ref) <= 5e-6, (s, "run-time")
+        assert oracle.rel_l2(a, r) <= 1e-6, s
+
+
 def test_graph_replay_new_data_and_new_buffers():
     shapes = [(24, 32, 48), (64, 24, 96), (32, 32, 32), (48, 128, 24)]
     plan = Plan(dtype="f32", shapes=shapes)
