@@ -184,6 +184,19 @@ def l2_note(shape) -> str:
     return f"L2-influenced: the spectrum fits in the 129 MB L2 ({sizes}), no flush"
 
 
+def solve_dram_frac(passes_ms: dict, unknowns: int, ms_per_step: float, peak: float):
+    """Whole-solve DRAM rate as a fraction of the peak: the recorded ncu
+    bytes of every pass of one solve over the event-timed solve; None if a
+    pass has no record for the current sources."""
+    total = 0.0
+    for name in passes_ms:
+        t = recorded_traffic(name, unknowns)
+        if t is None:
+            return None
+        total += t
+    return (total / (ms_per_step * 1e-3) / 1e9) / peak if passes_ms else None
+
+
 def kernel_digest() -> str:
     h = hashlib.sha256()
     for f in TRAFFIC_SOURCES:
@@ -446,6 +459,7 @@ def run_ours(args):
                      "algorithmic_bytes_per_launch": algo_bytes},
         "passes_ms": {k: round(v, 5) for k, v in avg.items()},
         "min_traffic_frac": (8 * N / (ms_per_step * 1e-3) / 1e9) / peak,
+        "solve_dram_frac": solve_dram_frac(avg, N, ms_per_step, peak),
         "e2e": {"value": ws * N / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 4 * N,
                 "d2h_bytes_per_step": 4 * N, "api": f"psolve_execute_host_async, pinned buffers, {NS} streams",
                 "runs_ms": [round(r * 1e3, 4) for r in runs], "sync_call_value": ws * N / e2e_sync_s},

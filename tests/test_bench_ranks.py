@@ -85,3 +85,14 @@ def test_traffic_record_matches_current_sources_or_is_dropped(monkeypatch):
     # a record keyed to other sources is not used
     monkeypatch.setattr(b, "kernel_digest", lambda: "0000000000000000")
     assert b.recorded_traffic("xdiv", 512 ** 3) is None
+
+
+def test_solve_dram_frac_sums_every_pass_or_is_none():
+    b = _bench()
+    passes = {"zfwd": 0.17, "yfwd": 0.17, "xdiv": 0.27, "yinv": 0.17, "zinv": 0.17}
+    frac = b.solve_dram_frac(passes, 512 ** 3, 0.94, 6793.8)
+    if b.recorded_traffic("xdiv", 512 ** 3) is not None:
+        # five passes of about 1.03 GB each in 0.94 ms: about 0.8 of 6.79 TB/s
+        assert 0.7 < frac < 0.9
+    assert b.solve_dram_frac(dict(passes, other=0.1), 512 ** 3, 0.94, 6793.8) is None
+    assert b.solve_dram_frac({}, 512 ** 3, 0.94, 6793.8) is None
