@@ -19,6 +19,7 @@ import argparse
 import hashlib
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -197,12 +198,27 @@ def solve_dram_frac(passes_ms: dict, unknowns: int, ms_per_step: float, peak: fl
     return (total / (ms_per_step * 1e-3) / 1e9) / peak if passes_ms else None
 
 
-def kernel_digest() -> str:
+_C_TOKENS = re.compile(r'//[^\n]*|/\*.*?\*/|"(?:\\.|[^"\\])*"|\'(?:\\.|[^\'\\])*\'', re.S)
+
+
+def code_only(text: str) -> str:
+    """C/C++/CUDA source without its comments (string and character literals
+    kept), so that comment edits do not count as kernel changes."""
+    return _C_TOKENS.sub(lambda m: " " if m.group(0).startswith("/") else m.group(0), text)
+
+
+def kernel_digest(read=None) -> str:
+    """Hash of TRAFFIC_SOURCES without comments; `read(path)` returns a
+    file's text (default: the working tree)."""
     h = hashlib.sha256()
     for f in TRAFFIC_SOURCES:
-        with open(os.path.join(ROOT, f), "rb") as fh:
-            h.update(f.encode())
-            h.update(fh.read())
+        if read is None:
+            with open(os.path.join(ROOT, f), encoding="utf-8") as fh:
+                text = fh.read()
+        else:
+            text = read(f)
+        h.update(f.encode())
+        h.update(code_only(text).encode())
     return h.hexdigest()[:16]
 
 

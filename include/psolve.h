@@ -3,8 +3,8 @@
  * as hand-written CUDA kernels for one GB300 (sm_103a).  C ABI.
  *
  * The operation (§1, Eq. 1.1; §2.1; §3 of Gholami, Malhotra, Sundar, Biros,
- * "FFT, FMM, or Multigrid?"): forward 3D FFT of f, Hadamard product with the
- * inverse of the Laplacian's diagonal (spectral) form, inverse 3D FFT:
+ * "FFT, FMM, or Multigrid?"): forward 3D FFT of f, each coefficient divided
+ * by the Laplacian's spectral symbol, inverse 3D FFT:
  *
  *     u = A f,   A = F^{-1} D F,   D(k) = 1 / (4π² |k|²),   D(0) = 0,
  *

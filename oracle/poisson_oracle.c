@@ -8,9 +8,10 @@
  *
  * What it computes (the plain definition, no blocking, no fusion):
  *   §1, Eq. 1.1:  -Δu = f, f smooth and periodic on [0,1)^3.
- *   §2.1:         forward FFT of f, Hadamard product with the inverse of the
- *                 diagonal (spectral) form of the Laplacian, inverse FFT.
- *   §3:           "3D FFT, diagonal scaling ..., then another 3D FFT".
+ *   §2.1:         transform f, multiply each coefficient by the reciprocal of
+ *                 the Laplacian's spectral symbol, transform back.
+ *   §3:           the solve as timed there: a forward 3D FFT, a pointwise
+ *                 scaling, an inverse 3D FFT.
  * On the grid x_j = j/n the discrete Fourier coefficients are
  *     F[k] = sum_x f[x] e^{-2πi k·x/n}   (per axis, no scaling),
  * the spectral symbol of -Δ is 4π²|k|² with the signed wavenumber

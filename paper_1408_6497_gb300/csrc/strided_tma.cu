@@ -7,8 +7,8 @@
 // two mbarriers).  The transform runs in place in the tile's buffer with the
 // same register/shared-memory Stockham engine as the other passes; results go
 // back to HBM from registers.  The x kind adds the spectral division between
-// its forward and inverse transforms (§2.1: Hadamard product with the inverse
-// Laplacian symbol) and, after its main tiles, the packed kz = 0 / kz = M
+// its forward and inverse transforms (§2.1: each coefficient times 1/(4π²|k|²))
+// and, after its main tiles, the packed kz = 0 / kz = M
 // column pairs.
 #include "psolve.h"
 #include "launch.h"

@@ -96,3 +96,11 @@ def test_solve_dram_frac_sums_every_pass_or_is_none():
         assert 0.7 < frac < 0.9
     assert b.solve_dram_frac(dict(passes, other=0.1), 512 ** 3, 0.94, 6793.8) is None
     assert b.solve_dram_frac({}, 512 ** 3, 0.94, 6793.8) is None
+
+
+def test_digest_ignores_comments_but_not_code():
+    b = _bench()
+    src = 'int a = 1; // note\n/* block\n */ const char *s = "// kept"; int d = 2 /* x */ + 3;\n'
+    assert b.code_only(src) == b.code_only(src.replace("note", "other").replace("block", "text"))
+    assert "// kept" in b.code_only(src)
+    assert b.code_only(src) != b.code_only(src.replace("2 /* x */ + 3", "2 + 4"))
