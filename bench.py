@@ -56,7 +56,8 @@ def parse():
                          "7-point finite-difference Laplacian; same passes, another multiplier")
     ap.add_argument("--helmholtz-c", type=float, default=1.0)
     ap.add_argument("--check", action="store_true",
-                    help="also report this run's rel-L2 against the FP64 oracle (a few s of CPU)")
+                    help="also report this run's rel-L2 against the FP64 oracle (a few s of CPU; "
+                         "batch64: worst and median over the 64 grids, batched and one plan per grid)")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--oracle-threads", type=int, default=0,
                     help="--impl reference: OpenMP threads of the FP64 oracle (0: all host cores)")
@@ -501,6 +502,12 @@ def run_ours(args):
 
 
 # ------------------------------------------------------------ batch of 64
+def batch_errors(oracle, fs, us):
+    """rel-L2 of each instance's solution `us[b]` against the FP64 oracle
+    solve of the same (FP32-rounded) right-hand side `fs[b]`."""
+    return [oracle.rel_l2(u, oracle.solve(np.asarray(f, dtype=np.float64))) for f, u in zip(fs, us)]
+
+
 def run_batch(args):
     """64 uneven grids (axes from {24..256}) per step in one persistent launch,
     next to the same 64 solves issued one plan per instance (the plain FP32
@@ -576,6 +583,18 @@ def run_batch(args):
         "gpu_launches": plan.launches_per_solve * args.steps,
         "clocks": clocks,
     }
+    if args.check and rank == 0:
+        import oracle
+        oracle.build()
+        u2 = torch.empty_like(flat)
+        plan.execute(flat, u)
+        for b, sp in enumerate(singles):
+            sp.execute(views_f[b], plan.view(u2, b).reshape(-1))
+        torch.cuda.synchronize(dev)
+        fs = [plan.view(flat, b).cpu().numpy() for b in range(64)]
+        for key, out in (("rel_l2_vs_oracle", u), ("single_solve_loop_rel_l2_vs_oracle", u2)):
+            errs = batch_errors(oracle, fs, [plan.view(out, b).cpu().numpy() for b in range(64)])
+            line[key] = {"worst": max(errs), "median": statistics.median(errs)}
     if rank == 0:
         print(json.dumps(line), flush=True)
     return 0

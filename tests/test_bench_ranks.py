@@ -104,3 +104,17 @@ def test_digest_ignores_comments_but_not_code():
     assert b.code_only(src) == b.code_only(src.replace("note", "other").replace("block", "text"))
     assert "// kept" in b.code_only(src)
     assert b.code_only(src) != b.code_only(src.replace("2 /* x */ + 3", "2 + 4"))
+
+
+def test_batch_errors_against_the_oracle():
+    import numpy as np
+    import oracle
+    oracle.build()
+    b = _bench()
+    rng = np.random.default_rng(5)
+    fs = [rng.standard_normal(s).astype(np.float32) for s in ((8, 12, 6), (6, 4, 8))]
+    exact = [oracle.solve(f.astype(np.float64)) for f in fs]
+    assert max(b.batch_errors(oracle, fs, exact)) < 1e-14
+    wrong = [exact[0], exact[1] * 1.01]
+    errs = b.batch_errors(oracle, fs, wrong)
+    assert errs[0] < 1e-14 and abs(errs[1] - 0.01) < 1e-9
