@@ -311,15 +311,9 @@ def run_reference_batch(args, oracle, wl, ws, rank):
     m as large as lets warmup + steps end within about two minutes."""
     shapes = wl.batch_shapes(64)
     fs = [wl.batch_instance(s, b).f for b, s in enumerate(shapes)]
-    t0 = time.perf_counter()
-    oracle.solve(fs[0])
-    per_unknown = (time.perf_counter() - t0) / fs[0].size
-    budget = 120.0 / max(1, args.steps + args.warmup)
-    m, n = 0, 0
-    while m < len(fs) and (m == 0 or (n + fs[m].size) * per_unknown <= budget):
-        n += fs[m].size
-        m += 1
+    m = batch_sample_size(oracle, fs, 120.0 / max(1, args.steps + args.warmup))
     sample = fs[:m]
+    n = sum(f.size for f in sample)
     for _ in range(args.warmup):
         for f in sample:
             oracle.solve(f)
@@ -502,6 +496,19 @@ def run_ours(args):
 
 
 # ------------------------------------------------------------ batch of 64
+def batch_sample_size(oracle, fs, budget_s: float) -> int:
+    """How many leading grids of `fs` one oracle pass solves within about
+    `budget_s` seconds (at least one), from the time of the first."""
+    t0 = time.perf_counter()
+    oracle.solve(fs[0])
+    per_unknown = (time.perf_counter() - t0) / fs[0].size
+    m, n = 0, 0
+    while m < len(fs) and (m == 0 or (n + fs[m].size) * per_unknown <= budget_s):
+        n += fs[m].size
+        m += 1
+    return m
+
+
 def batch_errors(oracle, fs, us):
     """rel-L2 of each instance's solution `us[b]` against the FP64 oracle
     solve of the same (FP32-rounded) right-hand side `fs[b]`."""
@@ -583,6 +590,19 @@ def run_batch(args):
         "gpu_launches": plan.launches_per_solve * args.steps,
         "clocks": clocks,
     }
+    if ws == 1 and rank == 0 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        fs64 = [wl.batch_instance(s, b).f for b, s in enumerate(shapes)]
+        m = batch_sample_size(oracle, fs64, 15.0)
+        t0 = time.perf_counter()
+        for f in fs64[:m]:
+            oracle.solve(f)
+        el = time.perf_counter() - t0
+        n = sum(f.size for f in fs64[:m])
+        line["cpu_baseline"] = {"value": n / el, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+                                "sample": f"FP64 oracle solves of the first {m} of the 64 grids "
+                                          f"({n} unknowns, {el:.1f} s)"}
     if args.check and rank == 0:
         import oracle
         oracle.build()

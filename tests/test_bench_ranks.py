@@ -118,3 +118,13 @@ def test_batch_errors_against_the_oracle():
     wrong = [exact[0], exact[1] * 1.01]
     errs = b.batch_errors(oracle, fs, wrong)
     assert errs[0] < 1e-14 and abs(errs[1] - 0.01) < 1e-9
+
+
+def test_batch_sample_size_is_bounded_and_at_least_one():
+    import numpy as np
+    import oracle
+    oracle.build()
+    b = _bench()
+    fs = [np.zeros((16, 16, 16)) for _ in range(5)]
+    assert b.batch_sample_size(oracle, fs, 0.0) == 1
+    assert b.batch_sample_size(oracle, fs, 1e6) == 5
