@@ -186,13 +186,14 @@ def l2_note(shape) -> str:
     return f"L2-influenced: the spectrum fits in the 129 MB L2 ({sizes}), no flush"
 
 
-def solve_dram_frac(passes_ms: dict, unknowns: int, ms_per_step: float, peak: float):
+def solve_dram_frac(passes_ms: dict, unknowns: int, ms_per_step: float, peak: float,
+                    shape=(512, 512, 512), operator: str = "poisson"):
     """Whole-solve DRAM rate as a fraction of the peak: the recorded ncu
     bytes of every pass of one solve over the event-timed solve; None if a
     pass has no record for the current sources."""
     total = 0.0
     for name in passes_ms:
-        t = recorded_traffic(name, unknowns)
+        t = recorded_traffic(name, unknowns, shape, operator)
         if t is None:
             return None
         total += t
@@ -223,16 +224,18 @@ def kernel_digest(read=None) -> str:
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(pass_name: str, unknowns: int):
+def recorded_traffic(pass_name: str, unknowns: int, shape=(512, 512, 512), operator: str = "poisson"):
     """DRAM bytes per launch of the pass's kernel from the committed ncu
-    summary (profiles/ncu_traffic.json), scaled to `unknowns` if the capture
-    was smaller, and only if it was taken on the current kernel sources."""
+    summary (profiles/ncu_traffic.json), only for the kernels it was taken
+    on: the same grid (other grids run other line-length instantiations),
+    the Poisson multiplier (other operators have their own x-pass
+    instantiation) and the current kernel sources."""
     p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
-    if not os.path.exists(p):
+    if not os.path.exists(p) or operator != "poisson":
         return None
     with open(p) as fh:
         d = json.load(fh)
-    if d.get("kernel_digest") != kernel_digest():
+    if d.get("kernel_digest") != kernel_digest() or list(d.get("grid", [])) != list(shape):
         return None
     e = d.get("passes", {}).get(pass_name)
     if not e:
@@ -446,7 +449,7 @@ def run_ours(args):
     peak, peak_kind = peaks()
     algo_bytes = BYTES_PER_UNKNOWN_PER_PASS * N
     achieved = algo_bytes / (avg[top] * 1e-3) / 1e9
-    traffic = recorded_traffic(top, N)
+    traffic = recorded_traffic(top, N, shape, args.operator)
 
     if rank != 0:
         if dist is not None:
@@ -470,7 +473,7 @@ def run_ours(args):
                      "algorithmic_bytes_per_launch": algo_bytes},
         "passes_ms": {k: round(v, 5) for k, v in avg.items()},
         "min_traffic_frac": (8 * N / (ms_per_step * 1e-3) / 1e9) / peak,
-        "solve_dram_frac": solve_dram_frac(avg, N, ms_per_step, peak),
+        "solve_dram_frac": solve_dram_frac(avg, N, ms_per_step, peak, shape, args.operator),
         "e2e": {"value": ws * N / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 4 * N,
                 "d2h_bytes_per_step": 4 * N, "api": f"psolve_execute_host_async, pinned buffers, {NS} streams",
                 "runs_ms": [round(r * 1e3, 4) for r in runs], "sync_call_value": ws * N / e2e_sync_s},

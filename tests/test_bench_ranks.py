@@ -128,3 +128,11 @@ def test_batch_sample_size_is_bounded_and_at_least_one():
     fs = [np.zeros((16, 16, 16)) for _ in range(5)]
     assert b.batch_sample_size(oracle, fs, 0.0) == 1
     assert b.batch_sample_size(oracle, fs, 1e6) == 5
+
+
+def test_traffic_record_only_for_the_captured_kernels():
+    b = _bench()
+    if b.recorded_traffic("xdiv", 512 ** 3) is None:
+        pytest.skip("no record for the current sources")
+    assert b.recorded_traffic("xdiv", 256 ** 3, (256, 256, 256)) is None
+    assert b.recorded_traffic("xdiv", 512 ** 3, (512, 512, 512), "helmholtz") is None
