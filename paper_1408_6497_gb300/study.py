@@ -4,7 +4,7 @@ growing n until the relative ℓ∞ error (the paper's metric) reaches a target.
 The paper's claim to reproduce: each doubling of α doubles the points per
 axis the FFT solve needs (eight times the unknowns).
 
-    python -m paper_1408_6497_gb300.study [--alphas 10 20 40] [--target 4e-7]
+    python -m paper_1408_6497_gb300.study [--alphas 10 20 40] [--target 4e-7] [--radius 0.1]
 
 prints one JSON line per (α, n) and a summary line per α.
 """
@@ -23,8 +23,8 @@ from .solver import Plan
 GRIDS = (32, 48, 64, 96, 128, 192, 256, 384, 512)
 
 
-def solve_case(n: int, alpha: float, dtype: str = "f64") -> dict:
-    f, u = wl.sphere_layer((n, n, n), alpha)
+def solve_case(n: int, alpha: float, dtype: str = "f64", R: float = 0.1) -> dict:
+    f, u = wl.sphere_layer((n, n, n), alpha, R=R)
     np_t = np.float64 if dtype == "f64" else np.float32
     plan = Plan((n, n, n), dtype=dtype)
     ft = torch.from_numpy(f.astype(np_t).ravel()).cuda()
@@ -37,17 +37,18 @@ def solve_case(n: int, alpha: float, dtype: str = "f64") -> dict:
     plan.status()
     ue = u - u.mean()  # the periodic solve fixes u up to its mean
     err = float(np.abs(uN.cpu().numpy().reshape(n, n, n).astype(np.float64) - ue).max() / np.abs(ue).max())
-    return {"alpha": alpha, "n": n, "unknowns": n ** 3, "dtype": dtype, "rel_linf": err, "solve_ms": ms}
+    return {"alpha": alpha, "R": R, "n": n, "unknowns": n ** 3, "dtype": dtype, "rel_linf": err, "solve_ms": ms}
 
 
-def resolution(alphas=(10.0, 20.0, 40.0), target: float = 4e-7, dtype: str = "f64", grids=GRIDS):
+def resolution(alphas=(10.0, 20.0, 40.0), target: float = 4e-7, dtype: str = "f64", grids=GRIDS,
+               R: float = 0.1):
     """For each α, solve on growing grids until rel ℓ∞ <= target; returns
     (rows, {α: smallest n reaching the target or None})."""
     rows, need = [], {}
     for alpha in alphas:
         need[alpha] = None
         for n in grids:
-            r = solve_case(n, alpha, dtype)
+            r = solve_case(n, alpha, dtype, R)
             rows.append(r)
             print(json.dumps(r), flush=True)
             if r["rel_linf"] <= target:
@@ -61,10 +62,12 @@ def main(argv=None) -> int:
     ap.add_argument("--alphas", type=float, nargs="+", default=[10.0, 20.0, 40.0])
     ap.add_argument("--target", type=float, default=4e-7)
     ap.add_argument("--dtype", choices=["f64", "f32"], default="f64")
+    ap.add_argument("--radius", type=float, default=0.1,
+                    help="sphere radius R (not stated in the paper; 0.1 gives its Tables 8 and 9)")
     args = ap.parse_args(argv)
-    _, need = resolution(args.alphas, args.target, args.dtype)
+    _, need = resolution(args.alphas, args.target, args.dtype, R=args.radius)
     for alpha, n in need.items():
-        print(json.dumps({"alpha": alpha, "target_rel_linf": args.target,
+        print(json.dumps({"alpha": alpha, "R": args.radius, "target_rel_linf": args.target,
                           "points_per_axis_needed": n, "unknowns": None if n is None else n ** 3}), flush=True)
     return 0
 

@@ -194,19 +194,24 @@ def random_field(shape, seed: int) -> np.ndarray:
     return np.random.default_rng(seed).standard_normal(tuple(shape))
 
 
-def sphere_layer(shape, alpha: float, R: float = 0.25, centre: float = 0.5):
+def sphere_layer(shape, alpha: float, R: float = 0.1, centre: float = 0.5, rows=None):
     """The paper's second time-to-solution case (§3, Tables 8-9): the exact
     solution u = exp(-(r/R)^α), r the (minimum-image) distance to the cube's
     centre, a sharp layer at r = R, and its source f = -Δu in closed form:
     with s = (r/R)^α,  -Δu = (α s u / r²)(α + 1 - α s)  (radial Laplacian
-    u'' + 2u'/r).  For α >= 10 and R = 1/4, u and f vanish at the cube's faces
-    to far below double precision, so both are smooth periodic fields.
-    Returns (f, u) in float64."""
+    u'' + 2u'/r).  The paper does not state R; R = 0.1 gives the FFT figures
+    of its Tables 8 and 9 (Table 9's error at 384³ for α = 40, Table 8's
+    grids for α = 10 and 40).  For α >= 10 and R <= 1/4, u and f vanish at the
+    cube's faces to far below double precision, so both are smooth periodic
+    fields.  Returns (f, u) in float64; rows = (x0, x1) returns only the
+    x-slab x0 <= x < x1 (for grids too large to evaluate at once)."""
     axes = []
     for n in shape:
         d = np.arange(n) / n - centre
         d -= np.round(d)  # minimum image
         axes.append(d)
+    if rows is not None:
+        axes[0] = axes[0][rows[0]:rows[1]]
     r2 = axes[0][:, None, None] ** 2 + axes[1][None, :, None] ** 2 + axes[2][None, None, :] ** 2
     s = (r2 / (R * R)) ** (alpha / 2.0)
     u = np.exp(-s)

@@ -1,13 +1,19 @@
 """The sharp-layer case (§3 test case 2): the closed-form source against the
-FP64 oracle, and the resolution trend the paper states (CPU only)."""
+FP64 oracle, the resolution trend the paper states, and the sphere's radius
+fixed by the FFT figures of Tables 8 and 9 (CPU only).  The generic checks
+use R = 1/4, whose wider layer is resolved on cheap grids."""
+import os
+
 import numpy as np
 import pytest
 
 from paper_1408_6497_gb300 import workloads as wl
 
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_table8_9_fft.txt")
 
-def _err(oracle_mod, n, alpha):
-    f, u = wl.sphere_layer((n, n, n), alpha)
+
+def _err(oracle_mod, n, alpha, R=0.25):
+    f, u = wl.sphere_layer((n, n, n), alpha, R=R)
     uN = oracle_mod.solve(f)
     ue = u - u.mean()  # the periodic solve fixes u up to its mean
     return np.abs(uN - ue).max() / np.abs(ue).max()
@@ -30,3 +36,35 @@ def test_doubling_alpha_needs_twice_the_points_per_axis(oracle_mod):
     e1, e2 = _err(oracle_mod, 32, 10.0), _err(oracle_mod, 64, 20.0)
     assert 0.05 < e2 / e1 < 20.0
     assert _err(oracle_mod, 32, 20.0) > 10 * e2  # not enough points for 2α
+
+
+def _golden():
+    t8, t9 = {}, None
+    with open(GOLDEN) as fh:
+        for line in fh:
+            parts = line.split()
+            if not parts or parts[0].startswith("#"):
+                continue
+            if parts[0] == "table8":
+                t8[float(parts[2])] = float(parts[3])
+            elif parts[0] == "table9":
+                t9 = (float(parts[1]), float(parts[2]), float(parts[3]))
+    return t8, t9
+
+
+def test_paper_tables_8_and_9_fix_the_radius(oracle_mod):
+    """The paper leaves R unstated.  R = 0.1 about the cube's centre gives
+    its FFT figures: Table 9's error at N = 5.6E+7 (384³) for α = 40, and
+    Table 8's N for α = 10 as the first grid of 128, 192, 256 points per
+    axis with a relative ℓ∞ error below 4E-7.  R = 1/4 misses Table 9's
+    error by orders of magnitude."""
+    t8, (a9, n9, e9) = _golden()
+    # the 2^a 3^b grid whose cube is nearest to the printed N (384 points per axis)
+    sizes = [2 ** a * 3 ** b for a in range(12) for b in range(7) if 2 ** a * 3 ** b <= 2048]
+    n = min(sizes, key=lambda m: abs(m ** 3 - n9))
+    assert n ** 3 == pytest.approx(n9, rel=0.02)
+    assert _err(oracle_mod, n, a9, R=0.1) == pytest.approx(e9, rel=0.1)
+    assert _err(oracle_mod, n, a9, R=0.25) < 1e-2 * e9
+    errs = {m: _err(oracle_mod, m, 10.0, R=0.1) for m in (128, 192, 256)}
+    first = min(m for m, e in errs.items() if e < 4e-7)
+    assert first ** 3 == pytest.approx(t8[10.0], rel=0.05)
