@@ -68,3 +68,18 @@ def test_paper_tables_8_and_9_fix_the_radius(oracle_mod):
     errs = {m: _err(oracle_mod, m, 10.0, R=0.1) for m in (128, 192, 256)}
     first = min(m for m, e in errs.items() if e < 4e-7)
     assert first ** 3 == pytest.approx(t8[10.0], rel=0.05)
+
+
+def test_study_host_steps_match_the_whole_grid(oracle_mod):
+    # the study builds f and measures the error slab by slab; same numbers as
+    # the whole-grid evaluation (48 planes: one full slab and a ragged one)
+    from paper_1408_6497_gb300 import study
+    n, alpha = 48, 10.0
+    f, u = wl.sphere_layer((n, n, n), alpha)
+    fs, umean = study.source(n, alpha)
+    np.testing.assert_array_equal(fs, f)
+    assert umean == pytest.approx(u.mean(), rel=1e-14)
+    uN = oracle_mod.solve(f)
+    ue = u - u.mean()
+    whole = np.abs(uN - ue).max() / np.abs(ue).max()
+    assert study.rel_linf(uN, n, alpha, 0.1, umean) == pytest.approx(whole, rel=1e-12)
