@@ -75,3 +75,30 @@ def test_valid_plan_without_device_fails_loudly(lib):
 def test_binding_raises_when_library_missing(tmp_path):
     with pytest.raises(RuntimeError, match="no CPU fallback"):
         _lib.load(str(tmp_path / "libpsolve.so"))
+
+
+def test_noalloc_argument_checks_on_the_host(lib):
+    # every case below is refused before any CUDA call; the pointers are
+    # never dereferenced.  The call leaves psolve_last_error() alone (it sets
+    # no message, so it allocates nothing on the host either).
+    h = ctypes.c_void_p()
+    assert lib.psolve_plan_create(10, 8, 8, _lib.F32, 1, ctypes.byref(h)) == 2
+    before = lib.psolve_last_error()
+    assert before
+    a = ctypes.c_void_p(1 << 20)
+    b = ctypes.c_void_p((1 << 20) + (1 << 16))
+    F32, F64 = _lib.F32, _lib.F64
+    assert lib.psolve_execute_noalloc(8, 8, 8, 9, a, b, None) == 1            # unknown dtype
+    assert lib.psolve_execute_noalloc(8, 8, 8, _lib.F32_TC, a, b, None) == 1  # TC needs a plan
+    assert lib.psolve_execute_noalloc(10, 8, 8, F32, a, b, None) == 2         # 10 = 2·5
+    assert lib.psolve_execute_noalloc(8, 8, 4096, F32, a, b, None) == 2       # above 2048
+    # FP64 tables for nx + ny + nz = 4100 points: 65600 bytes > 64 KiB
+    assert lib.psolve_execute_noalloc(2048, 2048, 4, F64, a, b, None) == 2
+    assert lib.psolve_execute_noalloc(8, 8, 8, F32, None, b, None) == 1       # null f
+    assert lib.psolve_execute_noalloc(8, 8, 8, F32, a, None, None) == 1       # null u
+    odd = ctypes.c_void_p((1 << 20) + 8)
+    assert lib.psolve_execute_noalloc(8, 8, 8, F32, odd, b, None) == 1        # not 16-B aligned
+    # u starts 16 bytes into f's 2 KiB (8³ FP32): partial overlap
+    inside = ctypes.c_void_p((1 << 20) + 16)
+    assert lib.psolve_execute_noalloc(8, 8, 8, F32, a, inside, None) == 1
+    assert lib.psolve_last_error() == before
