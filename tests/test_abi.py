@@ -102,3 +102,22 @@ def test_noalloc_argument_checks_on_the_host(lib):
     inside = ctypes.c_void_p((1 << 20) + 16)
     assert lib.psolve_execute_noalloc(8, 8, 8, F32, a, inside, None) == 1
     assert lib.psolve_last_error() == before
+
+
+def test_every_plan_entry_point_rejects_a_null_plan(lib):
+    # answered on the host before any CUDA call (no device here)
+    for name in ("psolve_execute", "psolve_adjoint", "psolve_execute_host", "psolve_execute_host_async"):
+        assert getattr(lib, name)(None, None, None, None) == 1, name
+    assert lib.psolve_set_operator(None, 0, 0.0) == 1
+    assert lib.psolve_get_status(None, None) == 1
+    assert lib.psolve_debug_kvec(None, 0, None) == 1
+    assert lib.psolve_autotune(None, None) == 1
+    assert lib.psolve_set_profiling(None, 1) == 1
+    assert lib.psolve_pass_times(None, None, 0, None, None) == 1
+    assert lib.psolve_debug_set_wait(None, 0, 0) == 1
+    assert lib.psolve_pass_name(None, 0) is None
+    assert lib.psolve_launches_per_solve(None) == 0
+    assert b"invalid or destroyed plan" in lib.psolve_last_error()
+    # pointer checks of the plan-free helpers
+    assert lib.psolve_error_norms(None, None, 0, _lib.F32, None, None) == 1
+    assert lib.psolve_debug_tc_dft16(None, None, 0, 0, None) == 1
