@@ -178,7 +178,8 @@ static void transform_axis(cplx *a, int nx, int ny, int nz, int axis, int sign, 
     free(w);
 }
 
-/* 3D DFT of the interleaved (re, im) array in place.  sign = -1 forward,
+/* 3D DFT of the interleaved (re, im) array in place (the transform of §2.1
+ * written out: one 1D DFT per line along each axis).  sign = -1 forward,
  * +1 inverse; never scaled. */
 void oracle_dft3d(double *re_im, int nx, int ny, int nz, int sign, int direct)
 {
@@ -235,8 +236,8 @@ double oracle_op_inverse(int op, double c, int jx, int jy, int jz, int nx, int n
     return oracle_symbol_inverse(jx, jy, jz, nx, ny, nz);
 }
 
-/* u = F^{-1}[ F[f] · multiplier(op) ]; op 0 gives the Poisson solve
- * u = F^{-1}[ F[f] / (4π²|k|²) ], û(0) = 0.  Returns 0 on success, -1 on
+/* u = F^{-1}[ F[f] · multiplier(op) ]; op 0 gives the Poisson solve of
+ * §2.1 (the three steps §3 times) u = F^{-1}[ F[f] / (4π²|k|²) ], û(0) = 0.  Returns 0 on success, -1 on
  * allocation failure.  *max_imag receives max |Im u| before it is dropped. */
 int oracle_solve_op(const double *f, double *u, int nx, int ny, int nz, int direct, int op, double c,
                     double *max_imag)
