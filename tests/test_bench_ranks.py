@@ -136,3 +136,19 @@ def test_traffic_record_only_for_the_captured_kernels():
         pytest.skip("no record for the current sources")
     assert b.recorded_traffic("xdiv", 256 ** 3, (256, 256, 256)) is None
     assert b.recorded_traffic("xdiv", 512 ** 3, (512, 512, 512), "helmholtz") is None
+
+
+def test_clock_rows_parsed_with_throttle_reasons():
+    b = _bench()
+    rows = "\n".join([
+        "0, 2070, 2070, 900.1, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "0, 1980, 2070, 1390.5, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+        "0, 2070, 2070, 1200.0, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "0, [N/A], 2070, 10.0, 0x0, Not Active, Not Active, Not Active, Not Active",  # skipped
+        "garbage",
+    ])
+    c = b.parse_clocks(rows)
+    assert c == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
+    hot = rows.replace("Not Active, Not Active, Not Active, Active", "Active, Not Active, Active, Not Active")
+    assert b.parse_clocks(hot)["reasons"] == ["hw_slowdown", "sw_thermal_slowdown"]
+    assert b.parse_clocks("")["sm_mhz"] is None
