@@ -152,3 +152,10 @@ def test_clock_rows_parsed_with_throttle_reasons():
     hot = rows.replace("Not Active, Not Active, Not Active, Active", "Active, Not Active, Active, Not Active")
     assert b.parse_clocks(hot)["reasons"] == ["hw_slowdown", "sw_thermal_slowdown"]
     assert b.parse_clocks("")["sm_mhz"] is None
+
+
+def test_cpu_baseline_leg_times_the_oracle():
+    b = _bench()
+    rate, t, reps, cores = b.oracle_rate(16, max_seconds=0.2, min_reps=2)
+    assert reps >= 2 and t > 0 and cores >= 1
+    assert rate == pytest.approx(16 ** 3 / t)
