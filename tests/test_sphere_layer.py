@@ -83,3 +83,19 @@ def test_study_host_steps_match_the_whole_grid(oracle_mod):
     ue = u - u.mean()
     whole = np.abs(uN - ue).max() / np.abs(ue).max()
     assert study.rel_linf(uN, n, alpha, 0.1, umean) == pytest.approx(whole, rel=1e-12)
+
+
+def test_study_ladder_stops_at_the_first_grid_below_target(monkeypatch):
+    from paper_1408_6497_gb300 import study
+    calls = []
+
+    def fake(n, alpha, dtype="f64", R=0.1):
+        calls.append((alpha, n))
+        return {"alpha": alpha, "n": n, "rel_linf": (alpha / n) ** 4}  # falls with n, rises with α
+
+    monkeypatch.setattr(study, "solve_case", fake)
+    rows, need = study.resolution(alphas=(10.0, 40.0), target=1e-6, grids=(32, 64, 128, 256, 512))
+    # (10/n)^4 <= 1e-6 needs n >= 317, so 512; (40/n)^4 needs n >= 1265: none
+    assert need == {10.0: 512, 40.0: None}
+    assert calls[:5] == [(10.0, 32), (10.0, 64), (10.0, 128), (10.0, 256), (10.0, 512)]
+    assert len(rows) == 10
