@@ -43,7 +43,8 @@ typedef enum {
     PSOLVE_F64 = 0,     /* double in, double out, FP64 butterflies          */
     PSOLVE_F32 = 1,     /* float in, float out, FP32 butterflies            */
     PSOLVE_F32_TC = 2   /* float in/out; radix-16 stages of the y and x passes on the tensor
-                           cores (tcgen05, BF16 hi/lo operands, FP32 accumulation in TMEM)
+                           cores (tcgen05; FP16 hi/lo operands with a power-of-two scale
+                           per butterfly row, FP32 accumulation in TMEM)
                            where those passes use the TMA kernels (lines of 256, 512 or 1024
                            points); every other stage in FP32.  Lines of 512 points use the
                            plan 32 × 16 by default (radix-32 stage in FP32, the radix-16
@@ -246,8 +247,8 @@ psolve_status psolve_execute_noalloc(int nx, int ny, int nz, int dtype, const vo
 /* Test hook for the tensor-core radix-16 stage used by PSOLVE_F32_TC: for
  * each of `nbutterflies` rows of 16 complex FP32 values (in, device,
  * interleaved re/im, row-major), out = F·in with F[k][r] = e^{-2πi kr/16}
- * (inverse = 1: e^{+2πi kr/16}), computed as BF16 hi/lo products
- * accumulated in FP32 in tensor memory.  Synchronises `stream`.  Returns
+ * (inverse = 1: e^{+2πi kr/16}), computed as FP16 hi/lo products (each
+ * row scaled by a power of two first) accumulated in FP32 in tensor memory.  Synchronises `stream`.  Returns
  * PSOLVE_ERR_TIMEOUT if the tensor-core completion wait ran out. */
 psolve_status psolve_debug_tc_dft16(const void *in, void *out, int nbutterflies, int inverse, void *stream);
 

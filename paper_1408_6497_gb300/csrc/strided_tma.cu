@@ -44,9 +44,10 @@ template <int L, int CFG> struct TmaShape {
 };
 
 // KIND: 0 = y forward, 1 = y inverse, 2 = x forward + division + x inverse.
-// TC: radix-16 stages on the tensor cores (BF16 hi/lo, FP32 accumulation in
-// TMEM).  With 16 points per thread (plans 16·16·…) every radix-16 stage
-// runs there, the exchange buffer holding the BF16 operand rows (it has
+// TC: radix-16 stages on the tensor cores (FP16 hi/lo with a power-of-two
+// scale per row, FP32 accumulation in TMEM).  With 16 points per thread
+// (plans 16·16·…) every radix-16 stage runs there, the exchange buffer
+// holding the FP16 operand rows (it has
 // exactly their size: one 128-byte row per thread).  With 32 points per
 // thread (512 = 32 × 16) the radix-32 stage stays in FP32 and the radix-16
 // stage, the last, runs on the tensor cores per warpgroup (tc32_last_stage),

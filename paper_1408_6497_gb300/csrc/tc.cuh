@@ -4,21 +4,31 @@
 // complex inputs of butterfly (row) tid.  The stage computes, per row,
 //     b = F a,   F[k][r] = e^{∓2πi kr/16},
 // as the real product of the row [Re a | Im a] (32 values) with the 32×32
-// real form of F, [[Re F, -Im F], [Im F, Re F]], on the tensor cores:
-// operands in BF16 split as x = hi + lo (hi = bf16(x), lo = bf16(x - hi)),
-// accumulated in FP32 in tensor memory (TMEM) as hi·Fhi + hi·Flo + lo·Fhi
-// (the lo·lo term, ~2^-18 relative, is dropped).  Each thread reads its own
-// row of the accumulator back (tcgen05.ld 32x32b: warp w sees TMEM lanes
-// 32·(w mod 4) ..), so the outputs land where the FP32 butterfly would have
-// left them.
+// real form of F, [[Re F, -Im F], [Im F, Re F]], on the tensor cores.
+//
+// Operand format: FP16 hi + lo with a power-of-two scale per row.  Each
+// thread scales its own row so that its largest |value| lies in
+// [2^14, 2^15) (exact: a power of two), splits every value as
+// x = hi + lo (hi = fp16(x), lo = fp16(x - hi): 22 significant bits, the
+// residual at most 2^-22 |x|), and the DFT matrix is split the same way from
+// its FP64 values.  The tensor cores accumulate hi·Fhi + hi·Flo + lo·Fhi in
+// FP32 in tensor memory (TMEM); the dropped lo·Flo term is about 2^-22
+// relative.  Each thread reads its own accumulator row back (tcgen05.ld
+// 32x32b: warp w sees TMEM lanes 32·(w mod 4) ..) and undoes the scale, so
+// the outputs land where the FP32 butterfly would have left them.  The scale
+// keeps FP16's range (largest finite 65504, smallest normal 2^-14) around
+// every row whatever the magnitudes the transform has reached.  A CPU
+// emulation of one stage on unit-variance rows gives a relative L2 error of
+// 7.6e-8 for this format (FP32 arithmetic: 6.3e-8), against 3.1e-6 for BF16
+// hi/lo with the same three products, whose 2^-18 residual of x dominates.
 //
 // Shared-memory operands use the no-swizzle K-major canonical layout: core
-// matrices of 8 rows × 16 bytes (8 BF16), 128 bytes each, K-adjacent core
+// matrices of 8 rows × 16 bytes (8 FP16), 128 bytes each, K-adjacent core
 // matrices 128 B apart (leading byte offset) and 8-row groups 512 B apart
 // (stride byte offset) for K = 32.
 #pragma once
 
-#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include "fft_core.cuh"
 #include "tma.cuh"
@@ -27,10 +37,10 @@ namespace psolve {
 
 constexpr int kTcK = 32;             // real K (16 complex inputs)
 constexpr int kTcN = 32;             // real N (16 complex outputs)
-constexpr int kTcRowBytes = kTcK * 2; // one BF16 row of A
-constexpr int kTcFBytes = kTcN * kTcRowBytes; // one 32×32 BF16 matrix (2 KiB)
+constexpr int kTcRowBytes = kTcK * 2; // one FP16 row of A
+constexpr int kTcFBytes = kTcN * kTcRowBytes; // one 32×32 FP16 matrix (2 KiB)
 
-// Byte offset of element (row, k) of a K-major no-swizzle BF16 operand with K = 32.
+// Byte offset of element (row, k) of a K-major no-swizzle 16-bit operand with K = 32.
 __host__ __device__ constexpr int tc_offset(int row, int k)
 {
     return ((row >> 3) * 4 + (k >> 3)) * 128 + (row & 7) * 16 + (k & 7) * 2;
@@ -48,10 +58,10 @@ __device__ __forceinline__ uint64_t tc_smem_desc(const void *p, uint32_t lbo, ui
     return d;
 }
 
-// Instruction descriptor, kind::f16: D FP32, A and B BF16, both K-major,
-// N = 32, M = 128.
-constexpr uint32_t kTcIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kTcN >> 3) << 17) |
-                              ((uint32_t)(128 >> 4) << 24);
+// Instruction descriptor, kind::f16: D FP32 (bits 4-5 = 1), A and B FP16
+// (type fields at bits 7-9 and 10-12 = 0; A and B always share one type),
+// both K-major, N = 32, M = 128.
+constexpr uint32_t kTcIdesc = (1u << 4) | ((uint32_t)(kTcN >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
 
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
@@ -103,22 +113,51 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&r)[32])
     for (int i = 0; i < 32; ++i) r[i] = __uint_as_float(u[i]);
 }
 
-// Split x into BF16 hi + lo, packed two values per 32-bit word (x0 in the
-// low half): one paired conversion for hi, the exact residuals x - hi as a
-// packed difference, one paired conversion for lo.
-__device__ __forceinline__ void bf16_split2(float x0, float x1, uint32_t &hi, uint32_t &lo)
+// Power-of-two scale s of a row of 16 complex values that brings its largest
+// |component| m into [2^14, 2^15), and 1/s in *inv (both exact).  The
+// exponent of m is clamped to [-112, 113] so that s and 1/s stay normal
+// FP32 numbers: rows with m below 2^-112 keep fewer bits (a zero row is
+// harmless), rows with m at or above 2^114 would overflow FP16 and are
+// outside the supported range.
+__device__ __forceinline__ float tc_row_scale(const float2 (&a)[16], float &inv)
 {
-    const __nv_bfloat162 h = __floats2bfloat162_rn(x0, x1);
-    const float2 r = csub(make_float2(x0, x1), __bfloat1622float2(h));
-    const __nv_bfloat162 l = __floats2bfloat162_rn(r.x, r.y);
+    float m = 0.f;
+#pragma unroll
+    for (int k = 0; k < 16; ++k) m = fmaxf(m, fmaxf(fabsf(a[k].x), fabsf(a[k].y)));
+    int e = (int)((__float_as_uint(m) >> 23) & 0xFFu) - 127; // floor(log2 m) for normal m
+    e = max(-112, min(113, e));
+    inv = __uint_as_float((uint32_t)(127 - 14 + e) << 23);
+    return __uint_as_float((uint32_t)(127 + 14 - e) << 23);
+}
+
+// Split s·x into FP16 hi + lo, packed two values per 32-bit word (x0 in the
+// low half): the scaling is exact, hi is one paired conversion, the residual
+// s·x - hi is exact in FP32, and lo is one more paired conversion.
+__device__ __forceinline__ void f16_split2(float x0, float x1, float s, uint32_t &hi, uint32_t &lo)
+{
+    const float2 xs = cscale(make_float2(x0, x1), s);
+    const __half2 h = __floats2half2_rn(xs.x, xs.y);
+    const float2 r = csub(xs, __half22float2(h));
+    const __half2 l = __floats2half2_rn(r.x, r.y);
     hi = *reinterpret_cast<const uint32_t *>(&h);
     lo = *reinterpret_cast<const uint32_t *>(&l);
+}
+
+// One operand row [Re a | Im a] as FP16 hi/lo words (hi[0..7]: Re, hi[8..15]:
+// Im), scaled by s.
+__device__ __forceinline__ void tc_split_row(const float2 (&a)[16], float s, uint32_t (&hi)[16], uint32_t (&lo)[16])
+{
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        f16_split2(a[2 * i].x, a[2 * i + 1].x, s, hi[i], lo[i]);         // Re a
+        f16_split2(a[2 * i].y, a[2 * i + 1].y, s, hi[8 + i], lo[8 + i]); // Im a
+    }
 }
 
 // Shared state of a block's tensor-core stages.
 struct TcCtx {
     unsigned char *a_hi, *a_lo;   // 128·G rows × 64 B each
-    const unsigned char *f_hi[2]; // [forward, inverse] 32×32 BF16, hi part
+    const unsigned char *f_hi[2]; // [forward, inverse] 32×32 FP16, hi part
     const unsigned char *f_lo[2];
     uint32_t tmem;                // TMEM base (32·G columns)
     uint64_t *bar;                // MMA completion barrier
@@ -127,8 +166,9 @@ struct TcCtx {
     int *status;                  // device status word
 };
 
-// Build the four 32×32 BF16 DFT matrices (hi/lo × forward/inverse) in shared
-// memory, from FP64 sincospi; called by the whole block.
+// Build the four 32×32 FP16 DFT matrices (hi/lo × forward/inverse) in shared
+// memory, from FP64 sincospi: hi = fp16(F), lo = fp16(F - hi) with the
+// residual taken in FP64; called by the whole block.
 __device__ __forceinline__ void tc_build_dft16(unsigned char *f_hi_fwd, unsigned char *f_lo_fwd,
                                                unsigned char *f_hi_inv, unsigned char *f_lo_inv)
 {
@@ -144,13 +184,12 @@ __device__ __forceinline__ void tc_build_dft16(unsigned char *f_hi_fwd, unsigned
             else if (n < 16) v = -fi;
             else if (k < 16) v = fi;
             else v = c;
-            const float vf = (float)v;
-            const __nv_bfloat16 h = __float2bfloat16_rn(vf);
-            const __nv_bfloat16 l = __float2bfloat16_rn(vf - __bfloat162float(h));
+            const __half h = __float2half_rn((float)v);
+            const __half l = __float2half_rn((float)(v - (double)__half2float(h)));
             unsigned char *hp = inv ? f_hi_inv : f_hi_fwd;
             unsigned char *lp = inv ? f_lo_inv : f_lo_fwd;
-            *reinterpret_cast<__nv_bfloat16 *>(hp + tc_offset(n, k)) = h;
-            *reinterpret_cast<__nv_bfloat16 *>(lp + tc_offset(n, k)) = l;
+            *reinterpret_cast<__half *>(hp + tc_offset(n, k)) = h;
+            *reinterpret_cast<__half *>(lp + tc_offset(n, k)) = l;
         }
     }
 }
@@ -161,14 +200,11 @@ template <bool INV>
 __device__ __forceinline__ void tc_dft16(float2 (&a)[16], const TcCtx &ctx)
 {
     const int tid = threadIdx.x;
-    // 1. this row of A, split into BF16 hi/lo, four 16-byte chunks each
+    // 1. this row of A, scaled and split into FP16 hi/lo, four 16-byte chunks each
+    float inv_s;
     {
         uint32_t hi[16], lo[16];
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            bf16_split2(a[2 * i].x, a[2 * i + 1].x, hi[i], lo[i]);         // Re a
-            bf16_split2(a[2 * i].y, a[2 * i + 1].y, hi[8 + i], lo[8 + i]); // Im a
-        }
+        tc_split_row(a, tc_row_scale(a, inv_s), hi, lo);
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
             const int off = tc_offset(tid, 8 * c);
@@ -216,7 +252,7 @@ __device__ __forceinline__ void tc_dft16(float2 (&a)[16], const TcCtx &ctx)
     float r[32];
     tmem_ld32(taddr, r);
 #pragma unroll
-    for (int k = 0; k < 16; ++k) a[k] = make_float2(r[k], r[16 + k]);
+    for (int k = 0; k < 16; ++k) a[k] = cscale(make_float2(r[k], r[16 + k]), inv_s);
     tc_fence_before(); // these reads precede the next batch of MMAs
 }
 
@@ -265,7 +301,7 @@ __device__ __forceinline__ void tmem_ld64(uint32_t taddr, float (&r)[64])
 
 struct Tc32Ctx {
     unsigned char *op;            // operand rows: [warpgroup][butterfly b][hi, lo] × 8 KiB
-    const unsigned char *f_hi[2]; // [forward, inverse] 32×32 BF16 DFT matrices
+    const unsigned char *f_hi[2]; // [forward, inverse] 32×32 FP16 DFT matrices
     const unsigned char *f_lo[2];
     uint32_t tmem;                // TMEM base (64 columns per warpgroup)
     uint64_t *bar;                // one MMA completion barrier per warpgroup
@@ -273,7 +309,7 @@ struct Tc32Ctx {
     int *status;                  // device status word
 };
 
-constexpr int kTcOpBytes = 128 * kTcRowBytes; // one 128-row BF16 operand (8 KiB)
+constexpr int kTcOpBytes = 128 * kTcRowBytes; // one 128-row FP16 operand (8 KiB)
 
 // Last stage (radix 16, Ns = 32) of a 512-point line, v[m] = x[t + 16·m]
 // on entry (the exchanged radix-32 outputs) and out[t + 16·m] on exit, with
@@ -287,6 +323,7 @@ __device__ __forceinline__ void tc32_last_stage(float2 (&v)[32], int t, const fl
     const int tid = threadIdx.x, g = tid >> 7, rl = tid & 127;
     const unsigned char *fh = c.f_hi[INV ? 1 : 0];
     const unsigned char *fl = c.f_lo[INV ? 1 : 0];
+    float inv_s[NB]; // each butterfly row's scale, undone on the way back
     // Butterfly 0's MMAs run while butterfly 1's operand rows are formed.
 #pragma unroll
     for (int b = 0; b < NB; ++b) {
@@ -299,11 +336,7 @@ __device__ __forceinline__ void tc32_last_stage(float2 (&v)[32], int t, const fl
             a[r] = INV ? cmulc(v[b + r * NB], w) : cmul(v[b + r * NB], w);
         }
         uint32_t hi[16], lo[16];
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            bf16_split2(a[2 * i].x, a[2 * i + 1].x, hi[i], lo[i]);         // Re
-            bf16_split2(a[2 * i].y, a[2 * i + 1].y, hi[8 + i], lo[8 + i]); // Im
-        }
+        tc_split_row(a, tc_row_scale(a, inv_s[b]), hi, lo);
         unsigned char *oh = c.op + ((g * NB + b) * 2) * kTcOpBytes;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
@@ -332,11 +365,16 @@ __device__ __forceinline__ void tc32_last_stage(float2 (&v)[32], int t, const fl
             if (b == NB - 1) tc_commit(&c.bar[g]); // completion of both butterflies' MMAs
         }
     }
-    if (!mbar_wait_bounded(&c.bar[g], nphase & 1u, 2000000000ull)) {
+    const bool done = mbar_wait_bounded(&c.bar[g], nphase & 1u, 2000000000ull);
+    if (!done) {
         *c.abort = 1;
         atomicExch(c.status, 5 /* PSOLVE_ERR_TIMEOUT */);
     }
     ++nphase;
+    // After a timed-out wait the accumulator is not read: the MMAs may still
+    // be running (the kernel lets them drain before it frees TMEM).  The read
+    // is warp-collective, so a warp skips it as a whole.
+    if (!__all_sync(0xFFFFFFFFu, done)) return;
     tc_fence_after();
     const int wq = (tid >> 5) & 3; // TMEM lanes 32·wq .. 32·wq + 31 for this warp
     float r[64];
@@ -344,7 +382,7 @@ __device__ __forceinline__ void tc32_last_stage(float2 (&v)[32], int t, const fl
 #pragma unroll
     for (int b = 0; b < NB; ++b)
 #pragma unroll
-        for (int k = 0; k < 16; ++k) v[b + k * NB] = make_float2(r[32 * b + k], r[32 * b + 16 + k]);
+        for (int k = 0; k < 16; ++k) v[b + k * NB] = cscale(make_float2(r[32 * b + k], r[32 * b + 16 + k]), inv_s[b]);
     tc_fence_before(); // these reads precede the warpgroup's next MMAs
 }
 

@@ -3,6 +3,8 @@ host-side argument checks answer without a GPU (CPU only)."""
 import ctypes
 import os
 import re
+import subprocess
+import sys
 
 import pytest
 import torch
@@ -77,10 +79,11 @@ def test_binding_raises_when_library_missing(tmp_path):
         _lib.load(str(tmp_path / "libpsolve.so"))
 
 
-def test_noalloc_argument_checks_on_the_host(lib):
-    # every case below is refused before any CUDA call; the pointers are
-    # never dereferenced.  The call leaves psolve_last_error() alone (it sets
-    # no message, so it allocates nothing on the host either).
+def _noalloc_refusals():
+    """Every case below is refused before any CUDA call; the made-up
+    pointers are never dereferenced.  The call leaves psolve_last_error()
+    alone (it sets no message, so it allocates nothing on the host either)."""
+    lib = _lib.load()
     h = ctypes.c_void_p()
     assert lib.psolve_plan_create(10, 8, 8, _lib.F32, 1, ctypes.byref(h)) == 2
     before = lib.psolve_last_error()
@@ -102,6 +105,18 @@ def test_noalloc_argument_checks_on_the_host(lib):
     inside = ctypes.c_void_p((1 << 20) + 16)
     assert lib.psolve_execute_noalloc(8, 8, 8, F32, a, inside, None) == 1
     assert lib.psolve_last_error() == before
+
+
+def test_noalloc_argument_checks_on_the_host(lib):
+    # Run with no device visible, so that even a host check that stopped
+    # working could only end in a CUDA error, never in a launch on made-up
+    # addresses.
+    env = dict(os.environ, CUDA_VISIBLE_DEVICES="")
+    code = "import tests.test_abi as t; t._noalloc_refusals(); print('refusals ok')"
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True, text=True,
+                       timeout=300)
+    assert r.returncode == 0, r.stdout + r.stderr
+    assert "refusals ok" in r.stdout
 
 
 def test_every_plan_entry_point_rejects_a_null_plan(lib):

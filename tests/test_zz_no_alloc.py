@@ -5,16 +5,19 @@ memory-pool callback, frameworks that forbid allocation during a step, hosts
 that reserve all device memory up front) use this entry point: it keeps its
 twiddle tables in a fixed 64 KiB array inside the library instead of a plan.
 Its result must match psolve_execute's, call after call, even though every
-call reuses the same shared array.  This file is collected last on purpose.
+call reuses the same shared array, and the FP64 oracle's within the parity
+tolerances.  This file is collected last on purpose.
 """
-import ctypes
 
 import numpy as np
 import pytest
 import torch
 
+import oracle
 from paper_1408_6497_gb300 import Plan, _lib
 from paper_1408_6497_gb300 import workloads as wl
+
+from .tolerances import check
 
 pytestmark = pytest.mark.gpu
 
@@ -58,6 +61,8 @@ def test_noalloc_matches_planned_solve_on_consecutive_calls(lib, prec):
         u = noalloc_solve(lib, prec, shape, f)
         err = rel_l2(u, ref)
         assert err <= TOL[prec], (shape, prec, err)
+        check(u.cpu().numpy().reshape(shape), oracle.solve(f.cpu().numpy().astype(np.float64).reshape(shape)),
+              prec, shape)
 
 
 def test_noalloc_in_place_and_twice_in_a_row(lib):
@@ -75,10 +80,25 @@ def test_noalloc_in_place_and_twice_in_a_row(lib):
 
 def test_noalloc_rejects_grids_beyond_the_table_array(lib):
     # FP64 tables for nx + ny + nz = 4100 need 65600 bytes > 64 KiB: refused
-    # on the host before anything is enqueued (the pointers are never used).
-    fake = ctypes.c_void_p(1 << 20)
-    rc = lib.psolve_execute_noalloc(2048, 2048, 4, _lib.F64, fake, fake, None)
-    assert rc == 2
-    # the same grid in FP32 fits, as do sizes outside the solver's range: checked first
-    assert lib.psolve_execute_noalloc(10, 8, 8, _lib.F32, fake, fake, None) == 2
-    assert lib.psolve_execute_noalloc(8, 8, 8, _lib.F32_TC, fake, fake, None) == 1
+    # on the host before anything is enqueued.  Size and dtype checks come
+    # before the pointer checks, so null arrays are passed: a size check that
+    # stopped working would end in the null-pointer refusal, not a launch.
+    assert lib.psolve_execute_noalloc(2048, 2048, 4, _lib.F64, None, None, None) == 2
+    # sizes outside the solver's range (10 = 2·5) and the tensor-core dtype
+    # (which needs a plan) are refused the same way
+    assert lib.psolve_execute_noalloc(10, 8, 8, _lib.F32, None, None, None) == 2
+    assert lib.psolve_execute_noalloc(8, 8, 8, _lib.F32_TC, None, None, None) == 1
+
+
+@pytest.mark.parametrize("prec,shape", [("f32", (2048, 2048, 4)), ("f64", (2048, 1024, 8))])
+def test_noalloc_grids_near_the_table_limit(lib, prec, shape):
+    # FP32 (2048, 2048, 4): 4100 complex twiddles = 32.8 KB of the 64 KiB
+    # array (every FP32 grid fits); FP64 (2048, 1024, 8): 3080 complex
+    # twiddles = 49.3 KB, within the FP64 limit nx + ny + nz <= 4096
+    f = torch.from_numpy(wl.random_field(shape, seed=77).astype(NP[prec]).ravel()).cuda()
+    ref = Plan(shape, dtype=prec).execute(f)
+    for _ in range(2):
+        u = noalloc_solve(lib, prec, shape, f)
+        assert rel_l2(u, ref) <= TOL[prec]
+    check(u.cpu().numpy().reshape(shape), oracle.solve(f.cpu().numpy().astype(np.float64).reshape(shape)),
+          prec, shape)
