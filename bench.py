@@ -50,7 +50,7 @@ def parse():
                          "uneven radix-2/3 grids in one persistent launch per step")
     ap.add_argument("--precision", choices=["f32", "f32_tc"], default="f32",
                     help="f32: FP32 butterflies; f32_tc: radix-16 stages of the y/x passes on the "
-                         "tensor cores (BF16 hi/lo, FP32 accumulation)")
+                         "tensor cores (FP16 hi/lo, row-scaled, FP32 accumulation)")
     ap.add_argument("--operator", choices=["poisson", "helmholtz", "fd"], default="poisson",
                     help="operator the solve inverts: -Δu = f (default), -Δu + c·u = f, or the "
                          "7-point finite-difference Laplacian; same passes, another multiplier")
@@ -62,6 +62,9 @@ def parse():
     ap.add_argument("--oracle-threads", type=int, default=0,
                     help="--impl reference: OpenMP threads of the FP64 oracle (0: all host cores)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-compare", action="store_true",
+                    help="default line: leave out the tensor-core and batched records (and their "
+                         "oracle checks) that follow the FP32 timed region")
     return ap.parse_args()
 
 
@@ -169,12 +172,14 @@ def gpu_uuid(torch, dev):
 
 # Sources of the kernels whose DRAM traffic profiles/ncu_traffic.json records
 # (the z bulk and TMA y/x passes): their translation units, every header they
-# include, and the host code that picks their configurations and grids.
+# include, and the host code that picks their configurations and grids (the
+# planner, the tuner and the pass pipeline).
 TRAFFIC_SOURCES = ("paper_1408_6497_gb300/csrc/strided_tma.cu", "paper_1408_6497_gb300/csrc/zpass_bulk.cu",
                    "paper_1408_6497_gb300/csrc/launch.h", "paper_1408_6497_gb300/csrc/passes.cuh",
                    "paper_1408_6497_gb300/csrc/fft_core.cuh", "paper_1408_6497_gb300/csrc/tc.cuh",
-                   "paper_1408_6497_gb300/csrc/tma.cuh", "paper_1408_6497_gb300/csrc/api.cu",
-                   "include/psolve.h")
+                   "paper_1408_6497_gb300/csrc/tma.cuh", "paper_1408_6497_gb300/csrc/plan.h",
+                   "paper_1408_6497_gb300/csrc/planner.cu", "paper_1408_6497_gb300/csrc/tuner.cu",
+                   "paper_1408_6497_gb300/csrc/pipeline.cu", "include/psolve.h")
 
 
 L2_BYTES = 129e6  # GB300 L2
@@ -349,6 +354,108 @@ def run_reference_batch(args, oracle, wl, ws, rank):
 
 
 # ------------------------------------------------------------------ ours
+def timed_solves(torch, plan, f, u, steps, dev, stream, barrier, profile=True):
+    """K solves of `plan` timed with CUDA events on the launching stream,
+    after a 2 s soak that brings the clocks to steady state; nvidia-smi
+    samples the clocks over soak and timed region.  Returns (ms per solve,
+    {pass: mean ms} over the profiled solves, clock record)."""
+    sampler = ClockSampler(gpu_uuid(torch, dev))
+    sampler.start()
+    soak_end = time.perf_counter() + 2.0
+    while time.perf_counter() < soak_end:
+        for _ in range(20):
+            plan.execute(f, u)
+        torch.cuda.synchronize(dev)
+    # Per-pass events on every PROFILE_EVERY-th solve only: a recorded solve
+    # runs its passes strictly back to back, the others overlap each pass's
+    # set-up with the previous pass's drain.
+    if profile:
+        plan.set_profiling(PROFILE_EVERY)
+    barrier()
+    torch.cuda.synchronize(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        plan.execute(f, u)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier()
+    clocks = sampler.stop()
+    avg = {}
+    if profile:
+        plan.set_profiling(False)
+        pass_ms, nsol = plan.pass_times()
+        avg = {k: v / max(1, nsol) for k, v in pass_ms.items()}
+    return e0.elapsed_time(e1) / steps, avg, clocks
+
+
+def tc_record(torch, args, f, f_np, N, shape, dev, stream, barrier, peak, ref):
+    """The tensor-core form of the same solve (radix-16 stages of the y and x
+    passes on tcgen05, FP16 hi/lo operands), timed like the FP32 line, with
+    its rel-L2 and rel-ℓ∞ against the FP64 oracle."""
+    from paper_1408_6497_gb300 import Plan
+    plan = Plan(shape, dtype="f32_tc", device=dev)
+    if not args.no_autotune:
+        plan.autotune()
+    u = torch.empty_like(f)
+    for _ in range(max(3, args.warmup)):
+        plan.execute(f, u)
+    torch.cuda.synchronize(dev)
+    ms, avg, clocks = timed_solves(torch, plan, f, u, args.steps, dev, stream, barrier)
+    rec = {"precision": "f32_tc", "dtype": "f32+fp16x3-tc", "ms_per_step": ms, "value": N / (ms * 1e-3),
+           "unit": UNIT, "passes_ms": {k: round(v, 5) for k, v in avg.items()},
+           "solve_dram_frac": solve_dram_frac(avg, N, ms, peak, shape),
+           "min_traffic_frac": (8 * N / (ms * 1e-3) / 1e9) / peak,
+           "gpu_launches": plan.launches_per_solve * args.steps, "clocks": clocks}
+    if ref is not None:
+        plan.execute(f, u)
+        ut = u.cpu().numpy().reshape(shape)
+        import oracle
+        rec["rel_l2_vs_oracle"] = oracle.rel_l2(ut, ref)
+        rec["rel_linf_vs_oracle"] = oracle.rel_linf(ut, ref)
+    plan.close()
+    return rec
+
+
+def batch64_record(torch, args, dev, stream, barrier, peak, check):
+    """The 64 uneven radix-2/3 grids in one persistent launch per step (one
+    graph replay), timed like the FP32 line; worst and median rel-L2 of the
+    64 solutions against the FP64 oracle."""
+    from paper_1408_6497_gb300 import Plan
+    from paper_1408_6497_gb300 import workloads as wl
+    shapes = wl.batch_shapes(64)
+    N = sum(int(np.prod(s)) for s in shapes)
+    plan = Plan(dtype="f32", shapes=shapes, device=dev)
+    if not args.no_autotune:
+        plan.autotune()
+    flat = plan.empty()
+    fs = []
+    for b, s in enumerate(shapes):
+        fb = wl.batch_instance(s, b).f.astype(np.float32)
+        fs.append(fb)
+        plan.view(flat, b).copy_(torch.from_numpy(fb))
+    u = torch.empty_like(flat)
+    for _ in range(max(3, args.warmup)):
+        plan.execute(flat, u)
+    torch.cuda.synchronize(dev)
+    ms, _, clocks = timed_solves(torch, plan, flat, u, args.steps, dev, stream, barrier, profile=False)
+    algo = 5 * BYTES_PER_UNKNOWN_PER_PASS * N
+    rec = {"workload": "64 FP32 grids, axes drawn from {24,32,48,64,96,128,192,256}, 16 periodised "
+                       "Gaussians each, one persistent launch per step", "unknowns": N,
+           "ms_per_step": ms, "value": N / (ms * 1e-3), "unit": UNIT,
+           "solve_dram_frac": (algo / (ms * 1e-3) / 1e9) / peak,
+           "solve_dram_frac_basis": "algorithmic bytes (5 passes x 8 B per unknown) over the event time",
+           "gpu_launches": plan.launches_per_solve * args.steps, "clocks": clocks}
+    if check:
+        import oracle
+        plan.execute(flat, u)
+        errs = batch_errors(oracle, fs, [plan.view(u, b).cpu().numpy() for b in range(64)])
+        rec["rel_l2_vs_oracle"] = {"worst": max(errs), "median": statistics.median(errs)}
+    plan.close()
+    return rec
+
+
 def run_ours(args):
     import torch
     ws, rank, local = dist_env()
@@ -369,7 +476,8 @@ def run_ours(args):
     n = args.grid
     shape = (n, n, n)
     N = n ** 3
-    f_host = torch.from_numpy(wl.sharp_source(shape).f.astype(np.float32).ravel())
+    f_np = wl.sharp_source(shape).f.astype(np.float32)
+    f_host = torch.from_numpy(f_np.ravel())
     f_pin = f_host.pin_memory()
     u_pin = torch.empty_like(f_pin).pin_memory()
     f = f_pin.to(dev)
@@ -387,32 +495,7 @@ def run_ours(args):
         plan.execute(f, u)
     torch.cuda.synchronize(dev)
 
-    sampler = ClockSampler(gpu_uuid(torch, dev))
-    sampler.start()
-    soak_end = time.perf_counter() + 2.0
-    while time.perf_counter() < soak_end:  # bring clocks to steady state under load
-        for _ in range(20):
-            plan.execute(f, u)
-        torch.cuda.synchronize(dev)
-
-    # Per-pass events on every PROFILE_EVERY-th solve only: a recorded solve
-    # runs its passes strictly back to back, the others overlap each pass's
-    # set-up with the previous pass's drain.
-    plan.set_profiling(PROFILE_EVERY)
-    barrier()
-    torch.cuda.synchronize(dev)
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
-        plan.execute(f, u)
-    e1.record(stream)
-    torch.cuda.synchronize(dev)
-    barrier()
-    clocks = sampler.stop()
-    el_ms = e0.elapsed_time(e1)
-    plan.set_profiling(False)
-    pass_ms, nsol = plan.pass_times()
+    ms_step, avg, clocks = timed_solves(torch, plan, f, u, args.steps, dev, stream, barrier)
 
     # End to end through the public host-buffer API: every step reads its f
     # from pinned host memory and writes its u back to pinned host memory.
@@ -446,17 +529,27 @@ def run_ours(args):
     e2e_sync_s = (time.perf_counter() - h1) / 3
     barrier()
 
-    el_ms, e2e_s, e2e_sync_s = max_over_ranks(dist, [el_ms, e2e_s, e2e_sync_s], dev)
+    el_ms, e2e_s, e2e_sync_s = max_over_ranks(dist, [ms_step * args.steps, e2e_s, e2e_sync_s], dev)
 
     ms_per_step = el_ms / args.steps
     value = job_value(ws, N, ms_per_step)
-    avg = {k: v / max(1, nsol) for k, v in pass_ms.items()}
     top = max(avg, key=avg.get)
     peak, peak_kind = peaks()
     algo_bytes = BYTES_PER_UNKNOWN_PER_PASS * N
     achieved = algo_bytes / (avg[top] * 1e-3) / 1e9
     traffic = recorded_traffic(top, N, shape, args.operator)
 
+    # The comparison the metric asks for: the tensor-core and batched forms
+    # next to this plain FP32 single solve, each with its error against the
+    # FP64 oracle (the default line only; one GPU).
+    compare = (ws == 1 and args.precision == "f32" and args.operator == "poisson" and n == 512
+               and not args.no_compare)
+    check = args.check or compare
+    ref = None
+    if check and rank == 0:
+        import oracle
+        oracle.build()
+        ref = oracle.solve(f_np.astype(np.float64), op=args.operator, c=args.helmholtz_c)
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
@@ -465,7 +558,7 @@ def run_ours(args):
         "impl": "ours", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32" if args.precision == "f32" else "f32+bf16x3-tc",
+        "dtype": "f32" if args.precision == "f32" else "f32+fp16x3-tc",
         "data": "synthetic",
         "config": {"workload": WORKLOAD.replace("512^3", f"{shape[0]}^3"), "grid": list(shape),
                    "precision": args.precision,
@@ -486,13 +579,18 @@ def run_ours(args):
         "gpu_launches": plan.launches_per_solve * args.steps,
         "clocks": clocks,
     }
-    if args.check and rank == 0:
+    if ref is not None:
         import oracle
-        from paper_1408_6497_gb300 import workloads as wl2
         plan.execute(f, u)
-        ref = oracle.solve(wl2.sharp_source(shape).f.astype(np.float32).astype(np.float64), op=args.operator,
-                           c=args.helmholtz_c)
-        line["rel_l2_vs_oracle"] = oracle.rel_l2(u.cpu().numpy().reshape(shape), ref)
+        uh = u.cpu().numpy().reshape(shape)
+        line["rel_l2_vs_oracle"] = oracle.rel_l2(uh, ref)
+        line["rel_linf_vs_oracle"] = oracle.rel_linf(uh, ref)
+    if compare:
+        plan.close()
+        line["tc"] = tc_record(torch, args, f, f_np, N, shape, dev, stream, barrier, peak, ref)
+        line["tc"]["vs_fp32_single_solve"] = line["tc"]["value"] / value
+        line["batch64"] = batch64_record(torch, args, dev, stream, barrier, peak, True)
+        line["batch64"]["vs_fp32_single_solve"] = line["batch64"]["value"] / value
     if ws == 1 and not args.no_cpu_baseline:
         rate, t, reps, cores = oracle_rate(min(n, 256), max_seconds=20.0)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
