@@ -223,8 +223,12 @@ psolve_status psolve_debug_set_wait(psolve_plan *plan, unsigned long long wait_n
 /* Allocation-free solve, for callers that cannot allocate device memory:
  * code inside a custom allocator or memory-pool callback, frameworks that
  * forbid allocation during a step, hosts that reserve all device memory up
- * front.  The paper has no counterpart; it is psolve_execute for one grid
- * nx × ny × nz (same checks, same kernels, same result) without a plan.
+ * front.  The paper has no counterpart.  It solves one grid nx × ny × nz
+ * without a plan, with the same argument checks as psolve_execute and the
+ * per-tile pass kernels psolve_execute uses where its TMA and bulk-copy
+ * passes do not apply (those are not used here), with the planner's stage
+ * plans and tile shapes; results agree with psolve_execute's within the
+ * dtype's tolerance, not bit for bit.
  * It calls no cudaMalloc, cudaFree or other allocating routine.  The only
  * memory besides f and u is the twiddle tables, held in one fixed 64 KiB
  * device array inside the library (every GPU that loads the library keeps
@@ -235,8 +239,9 @@ psolve_status psolve_debug_set_wait(psolve_plan *plan, unsigned long long wait_n
  * dtype: PSOLVE_F32 or PSOLVE_F64 (else PSOLVE_ERR_INVALID_ARG).  f, u:
  * device pointers as for psolve_execute (u == f allowed).
  * The first call on each device looks up the array's device address with
- * that device current (cudaGetSymbolAddress); make it before any stream
- * capture.  Every call rewrites the whole array on `stream` before its
+ * that device current (cudaGetSymbolAddress) and keeps it; make that call
+ * before any stream capture.  Resetting the device (cudaDeviceReset) after
+ * that first call is not supported.  Every call rewrites the whole array on `stream` before its
  * kernels read it, so nothing carries over from the previous call, but calls
  * whose work overlaps on the GPU (different streams, no ordering) race on
  * the shared array and give wrong results: order them.

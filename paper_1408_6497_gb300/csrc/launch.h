@@ -100,6 +100,28 @@ bool fused_supported(int M, int ny);
 cudaError_t launch_fused_zy(const ZArgs<float> &az, const SArgs<float> &ay, const FusedArgs &fa, bool inverse,
                             size_t smem, cudaStream_t s);
 
+// z and y passes of a plane in one launch, the plane held in the distributed
+// shared memory of a 16-block cluster (FP32; ny = 256 or 512 rows of
+// M = 128 or 256 packed complex values).
+struct ZyArgs {
+    const float *real_in; // forward: f rows
+    float *real_out;      // inverse: u rows
+    float2 *spec;         // packed spectrum, natural layout (forward output; the inverse reads it by TMA)
+    long long planes;     // x-planes of all instances
+    const float2 *tw_y;   // e^{-2πi j/ny}
+    const float2 *tw_z;   // e^{-2πi j/M}
+    const float2 *post;   // e^{-2πi k/nz}, k < M
+    int *status;
+};
+bool zy_cluster_supported(int M, int ny);
+int zy_cluster_size();
+// Clusters of the kernel that fit on the device at once (0: none).
+cudaError_t zy_cluster_max_active(int M, int ny, bool inverse, int *clusters);
+// map: the spectrum as a 3D tensor (M, ny, planes) of 8-byte elements with
+// box (M / 16, min(ny, 256), 1), read by the inverse pass.
+cudaError_t launch_zy_cluster(const CUtensorMap &map, const ZyArgs &a, int M, int ny, bool inverse, int clusters,
+                              cudaStream_t s, bool pdl = true);
+
 // Persistent batched kernel: one segment per (pass, instance), pass-major.
 // Threads of a batched-launch block: 128, four blocks per SM (measured on
 // GB300 for the 64-grid batch: 1.36 ms against 1.51 ms with 256-thread blocks

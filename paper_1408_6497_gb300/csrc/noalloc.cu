@@ -4,13 +4,14 @@
 // allocator or memory-pool callback, code under a framework that forbids
 // allocation during a step (a capture or a fixed-memory budget), or embedded
 // hosts that pre-reserve all device memory.  For them this entry point runs
-// the same five pass kernels as psolve_execute without a plan: the only
+// the per-tile pass kernels of psolve_execute without a plan, with the same
+// stage plans and tile shapes the planner gives those kernels: the only
 // memory beyond the caller's f and u is the twiddle tables, and those live in
 // a fixed file-scope device array instead of plan-owned allocations.  Nothing
 // here calls cudaMalloc, cudaFree or any other allocating routine, on the
-// device or on the host (the planning below uses the stack only).
-#include "psolve.h"
-#include "launch.h"
+// device or on the host (the planner's line plans and tile choice use fixed
+// arrays on the stack).
+#include "plan.h"
 
 #include <cmath>
 #include <cstdint>
@@ -42,61 +43,9 @@ psolve_status err(psolve_status s, const char *reason)
     return s;
 }
 
-bool f23(int n, int &a, int &b)
-{
-    a = b = 0;
-    if (n <= 0) return false;
-    while (n % 2 == 0) { n /= 2; ++a; }
-    while (n % 3 == 0) { n /= 3; ++b; }
-    return n == 1;
-}
-
-bool valid_n(int n)
-{
-    int a, b;
-    return n >= 4 && n <= 2048 && (n % 2) == 0 && f23(n, a, b);
-}
-
-// Same stage plan as the planned path: radix-3 stages, then the largest
-// power-of-two radices (<= 16) dividing the points-per-thread E.
-bool line_plan(int L, LinePlan &p)
-{
-    int a, b;
-    if (!f23(L, a, b) || L < 2) return false;
-    const int E = b > 0 ? 3 * (1 << (a < 3 ? a : 3)) : (1 << (a < 4 ? a : 4));
-    if (!supported_E(E)) return false;
-    std::memset(&p, 0, sizeof(p));
-    p.L = L;
-    p.E = E;
-    p.TL = L / E;
-    int p2 = 1;
-    while (E % (p2 * 2) == 0 && p2 * 2 <= 16) p2 *= 2;
-    int rad[kMaxStages];
-    int n = 0;
-    for (int i = 0; i < b; ++i) rad[n++] = 3;
-    int rem = 1 << a;
-    while (rem > 1) {
-        if (n >= kMaxStages) return false;
-        const int r = p2 < rem ? p2 : rem;
-        rad[n++] = r;
-        rem /= r;
-    }
-    p.nst = n;
-    int ns = 1;
-    for (int s = 0; s < n; ++s) {
-        p.radix[s] = rad[s];
-        p.ns[s] = ns;
-        p.twstep[s] = L / (ns * rad[s]);
-        ns *= rad[s];
-    }
-    line_plan_finish(p);
-    return true;
-}
-
-constexpr size_t kSmemCap = 200 * 1024;
-
 // Device address of the table array on the current device, looked up once
-// per device (with that device current) and cached.
+// per device (with that device current, on the first call there) and cached;
+// a reset of that device after the first call is not supported.
 psolve_status table_address(void **out)
 {
     int dev = 0;
@@ -119,12 +68,20 @@ template <typename T>
 psolve_status run(int nx, int ny, int nz, const T *f, T *u, unsigned char *tables, cudaStream_t s)
 {
     using C = typename cplx_of<T>::type;
-    const bool fp64 = sizeof(T) == 8;
-    const size_t cs = sizeof(C);
+    const int dtype = sizeof(T) == 8 ? PSOLVE_F64 : PSOLVE_F32;
     const int M = nz / 2;
-    LinePlan pz, py, px;
-    if (!line_plan(M, pz) || !line_plan(ny, py) || !line_plan(nx, px))
+    // The planner's stage plans and tile widths (without the PSOLVE_TILE_W
+    // override), as psolve_execute's per-tile passes of this grid would use.
+    Group g{};
+    g.nx = nx;
+    g.ny = ny;
+    g.nz = nz;
+    g.M = M;
+    if (!make_line_plan(M, g.pz) || !make_line_plan(ny, g.py) || !make_line_plan(nx, g.px))
         return err(PSOLVE_ERR_UNSUPPORTED_SIZE, "no stage plan for this size");
+    choose_tiles(g, dtype, false);
+    const LinePlan &pz = g.pz, &py = g.py, &px = g.px;
+    const int Wz = g.Wz, Wy = g.Wy, Wx = g.Wx;
 
     // Table layout: [e^{-2πij/M}][e^{-2πij/ny}][e^{-2πij/nx}][e^{-2πik/nz}, k < M]
     const size_t o_z = 0, o_y = o_z + M, o_x = o_y + ny, o_p = o_x + nx;
@@ -134,35 +91,6 @@ psolve_status run(int nx, int ny, int nz, const T *f, T *u, unsigned char *table
     if (e == cudaSuccess) e = launch_roots<T>(tab + o_x, nx, nx, s);
     if (e == cudaSuccess) e = launch_roots<T>(tab + o_p, M, nz, s);
     if (e != cudaSuccess) return err(PSOLVE_ERR_CUDA, "twiddle generation launch failed");
-
-    // Tile shapes (as in the planned path).
-    int Wz = 1, Wy = 1, Wx = 2;
-    {
-        const int mt = max_threads(fp64, pz.E);
-        Wz = (mt < 256 ? mt : 256) / pz.TL;
-        if (Wz < 1) Wz = 1;
-        const int LP = M + (M >> 4) + 1;
-        while (Wz > 1 && (size_t)(M + (size_t)Wz * LP) * cs > kSmemCap) Wz /= 2;
-    }
-    {
-        const int mt = max_threads(fp64, py.E);
-        int W = mt / py.TL;
-        if (W < 1) W = 1;
-        if (W > 16) W = 16;
-        if (W > M) W = M;
-        while (W > 1 && (size_t)ny * (1 + W) * cs > kSmemCap) W /= 2;
-        Wy = W < 1 ? 1 : W;
-    }
-    {
-        const int mt = max_threads(fp64, px.E);
-        int W = mt / px.TL;
-        if (W < 2) W = 2;
-        if (W > 16) W = 16;
-        const int cap = M < 2 ? 2 : M;
-        if (W > cap) W = cap;
-        while (W > 2 && (size_t)nx * (1 + W) * cs > kSmemCap) W /= 2;
-        Wx = W;
-    }
 
     ZArgs<T> z{};
     z.in = f;
@@ -176,7 +104,7 @@ psolve_status run(int nx, int ny, int nz, const T *f, T *u, unsigned char *table
     z.post = tab + o_p;
     const unsigned zgrid = (unsigned)((z.rows + Wz - 1) / Wz);
     const unsigned zblock = (unsigned)(Wz * pz.TL);
-    const size_t zsm = (size_t)(M + (size_t)Wz * (M + (M >> 4) + 1)) * cs;
+    const size_t zsm = z_smem(g, dtype);
     if (launch_zfwd<T>(z, zgrid, zblock, zsm, s) != cudaSuccess) return err(PSOLVE_ERR_CUDA, "z forward pass");
 
     SArgs<T> y{};
@@ -191,7 +119,7 @@ psolve_status run(int nx, int ny, int nz, const T *f, T *u, unsigned char *table
     y.tw = tab + o_y;
     const unsigned ygrid = (unsigned)(y.nplanes * y.ncb);
     const unsigned yblock = (unsigned)(Wy * py.TL);
-    const size_t ysm = (size_t)ny * (1 + Wy) * cs;
+    const size_t ysm = s_smem(ny, Wy, dtype);
     if (launch_ypass<T>(y, false, ygrid, yblock, ysm, s) != cudaSuccess)
         return err(PSOLVE_ERR_CUDA, "y forward pass");
 
@@ -211,7 +139,7 @@ psolve_status run(int nx, int ny, int nz, const T *f, T *u, unsigned char *table
     x.coef = (T)(1.0 / (4.0 * M_PI * M_PI * ((double)nx * ny * nz)));
     const unsigned xgrid = (unsigned)(x.main_tiles + (x.npairs + Wx / 2 - 1) / (Wx / 2));
     const unsigned xblock = (unsigned)(Wx * px.TL);
-    if (launch_xfused<T>(x, xgrid, xblock, (size_t)nx * (1 + Wx) * cs, s) != cudaSuccess)
+    if (launch_xfused<T>(x, xgrid, xblock, s_smem(nx, Wx, dtype), s) != cudaSuccess)
         return err(PSOLVE_ERR_CUDA, "x pass with spectral division");
 
     if (launch_ypass<T>(y, true, ygrid, yblock, ysm, s) != cudaSuccess)
@@ -232,7 +160,7 @@ psolve_status psolve_execute_noalloc(int nx, int ny, int nz, int dtype, const vo
 {
     if (dtype != PSOLVE_F64 && dtype != PSOLVE_F32)
         return err(PSOLVE_ERR_INVALID_ARG, "psolve_execute_noalloc supports PSOLVE_F64 and PSOLVE_F32");
-    if (!valid_n(nx) || !valid_n(ny) || !valid_n(nz))
+    if (!size_ok(nx) || !size_ok(ny) || !size_ok(nz))
         return err(PSOLVE_ERR_UNSUPPORTED_SIZE, "each n must be 2^a 3^b, even, 4 <= n <= 2048");
     const size_t cs = dtype == PSOLVE_F64 ? 16 : 8;
     const size_t need = ((size_t)nz + ny + nx) * cs;

@@ -94,6 +94,59 @@ def test_fused_zy_parity_fp32(shape, monkeypatch):
     assert torch.equal(uu, u)
 
 
+# z rows of 256/512 points with y lines of 256/512 points: the z and y
+# transforms of a plane in one 16-block cluster's distributed shared memory
+# (three passes through HBM); 4 x-planes leave most clusters idle.
+CLUSTER_SHAPES = [(64, 512, 512), (32, 256, 256), (48, 512, 256), (24, 256, 512), (4, 512, 512),
+                  (512, 512, 512)]
+
+
+@pytest.mark.parametrize("shape", CLUSTER_SHAPES)
+def test_cluster_zy_parity_fp32(shape, monkeypatch):
+    monkeypatch.setenv("PSOLVE_FUSED", "16")
+    f64 = wl.random_field(shape, seed=850 + sum(shape))
+    plan = Plan(shape, dtype="f32")
+    names = [plan.lib.psolve_pass_name(plan.handle, i).decode() for i in range(3)]
+    assert names == ["zyfwd", "xdiv", "yzinv"]
+    assert plan.launches_per_solve == 3
+    f = torch.from_numpy(f64.astype(np.float32).ravel()).cuda()
+    u = plan.execute(f)
+    plan.status()
+    ref = oracle.solve(f.cpu().numpy().astype(np.float64).reshape(shape))
+    check(u.cpu().numpy().reshape(shape), ref, "f32", shape)
+    uu = f.clone()
+    plan.execute(uu, uu)  # in place
+    plan.status()
+    assert torch.equal(uu, u)
+
+
+def test_cluster_zy_batch_and_adjoint_fp32(monkeypatch):
+    monkeypatch.setenv("PSOLVE_FUSED", "16")
+    shape, B = (16, 512, 512), 3
+    f = np.stack([wl.random_field(shape, seed=95 + b) for b in range(B)])
+    u, f_in = gpu_solve(f, "f32", batch=B)
+    for b in range(B):
+        check(u[b], oracle.solve(f_in[b].astype(np.float64)), "f32")
+
+
+def test_cluster_zy_host_buffers(monkeypatch):
+    # host-buffer solves of a cluster plan: pinned buffers go through the
+    # five-pass path (the cluster kernels read f with bulk copies from device
+    # memory only), pageable ones through the staging buffer and the cluster
+    monkeypatch.setenv("PSOLVE_FUSED", "16")
+    shape = (32, 512, 256)
+    f = torch.from_numpy(wl.random_field(shape, seed=96).astype(np.float32).ravel())
+    plan = Plan(shape, dtype="f32")
+    u_dev = plan.execute(f.cuda()).cpu()
+    fp = f.pin_memory()
+    up = torch.empty_like(fp).pin_memory()
+    plan.execute_host(fp, up)
+    ref = oracle.solve(f.numpy().astype(np.float64).reshape(shape))
+    check(up.numpy().reshape(shape), ref, "f32")
+    u_pg = plan.execute_host(f.numpy())
+    assert np.array_equal(u_pg, u_dev.numpy())
+
+
 def test_fused_zy_batch_fp32(monkeypatch):
     monkeypatch.setenv("PSOLVE_FUSED", "4")
     shape, B = (32, 256, 512), 3
