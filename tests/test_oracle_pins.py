@@ -269,6 +269,22 @@ def test_fd_operator_limit_is_the_spectral_one(oracle_mod):
     assert 0 < oracle_mod.rel_l2(u_fd, u_sp) < 1e-3  # O(h²) apart
 
 
+@pytest.mark.parametrize("n,k", [(2048, 1), (2048, 3), (1458, 1), (1944, 2)])
+def test_fd_lowest_modes_of_fine_grids_to_full_precision(oracle_mod, n, k):
+    # A single mode cos(2πkx) of a fine grid is an eigenvector of the stencil
+    # with eigenvalue (2/h²)(1 − cos 2πk/n); evaluated in 40-digit arithmetic
+    # (mpmath, independent of the oracle), u = f/λ must hold to FP64 rounding.
+    # These are the modes a solve's u is made of, and the ones where the
+    # cosine form of λ loses digits to cancellation in FP64.
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 40
+    lam = float(2 * mp.mpf(n) ** 2 * (1 - mp.cos(2 * mp.pi * k / n)))
+    x = np.arange(n) / n
+    f = np.cos(2 * np.pi * k * x)[:, None, None] * np.ones((n, 4, 6))
+    u = oracle_mod.solve(f, op="fd")
+    assert np.abs(u - f / lam).max() <= 1e-14 * np.abs(f / lam).max()
+
+
 @pytest.mark.parametrize("c", [0.5, 3.7, 1e3])
 def test_helmholtz_modes_and_constant(oracle_mod, c):
     shape = (8, 12, 6)
