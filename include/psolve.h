@@ -57,7 +57,7 @@ typedef enum {
 typedef enum {
     PSOLVE_OK = 0,
     PSOLVE_ERR_INVALID_ARG = 1,      /* null/misaligned pointer, bad batch, bad dtype, partial overlap */
-    PSOLVE_ERR_UNSUPPORTED_SIZE = 2, /* an n is not 2^a 3^b, is odd, < 4 or > 2048                    */
+    PSOLVE_ERR_UNSUPPORTED_SIZE = 2, /* an n is not 2^a 3^b, is odd, < 4 or > 2048 (FP64: nx = 1458) */
     PSOLVE_ERR_OOM = 3,              /* device allocation failed                                       */
     PSOLVE_ERR_CUDA = 4,             /* a CUDA call failed (no device, launch error, ...)              */
     PSOLVE_ERR_TIMEOUT = 5,          /* a bounded device-side wait gave up                             */
@@ -85,7 +85,9 @@ typedef struct psolve_plan psolve_plan;
 
 /* Create a plan for `batch` equal grids nx × ny × nz (§3: the setup is paid
  * once and amortised over solves with new right-hand sides).  Each n must
- * be 2^a·3^b, even, 4 <= n <= 2048.  Allocates the plan's twiddle tables
+ * be 2^a·3^b, even, 4 <= n <= 2048; FP64 plans also reject nx = 1458
+ * (2·3^6: the x pass's tile of two such lines needs 486 threads, more than
+ * an FP64 block holds), with PSOLVE_ERR_UNSUPPORTED_SIZE.  Allocates the plan's twiddle tables
  * (computed on the device in FP64) and status word on the current device.
  * The spectrum is formed inside u itself, so no workspace of the grid's
  * size is allocated, except for FP32 grids whose x lines lie 4 MiB or more
@@ -234,7 +236,8 @@ psolve_status psolve_debug_set_wait(psolve_plan *plan, unsigned long long wait_n
  * device array inside the library (every GPU that loads the library keeps
  * it until the process exits); a grid needs (nx + ny + nz) complex values
  * there (8 B each in FP32, 16 B in FP64), so every valid FP32 grid fits and
- * an FP64 grid fits while nx + ny + nz <= 4096; larger grids return
+ * an FP64 grid fits while nx + ny + nz <= 4096; larger grids (and the
+ * sizes psolve_plan_create rejects, FP64 nx = 1458 included) return
  * PSOLVE_ERR_UNSUPPORTED_SIZE before anything is enqueued.
  * dtype: PSOLVE_F32 or PSOLVE_F64 (else PSOLVE_ERR_INVALID_ARG).  f, u:
  * device pointers as for psolve_execute (u == f allowed).

@@ -80,6 +80,7 @@ psolve_status run(int nx, int ny, int nz, const T *f, T *u, unsigned char *table
     if (!make_line_plan(M, g.pz) || !make_line_plan(ny, g.py) || !make_line_plan(nx, g.px))
         return err(PSOLVE_ERR_UNSUPPORTED_SIZE, "no stage plan for this size");
     choose_tiles(g, dtype, false);
+    if (!tiles_fit(g, dtype)) return err(PSOLVE_ERR_UNSUPPORTED_SIZE, "no tile of this grid fits a block");
     const LinePlan &pz = g.pz, &py = g.py, &px = g.px;
     const int Wz = g.Wz, Wy = g.Wy, Wx = g.Wx;
 

@@ -68,6 +68,9 @@ size_t rsize(int dtype);
 int zpitch(int M);
 size_t z_smem(const Group &g, int dtype);
 size_t s_smem(int L, int W, int dtype);
+// Whether every per-tile pass of group g fits a block with its chosen tile
+// widths (the x pass needs two columns: FP64 x lines of 1458 points do not).
+bool tiles_fit(const Group &g, int dtype);
 // Whether the z/y fusion with cluster size `fused` can run for group g.
 bool fused_ok(const Group &g, int dtype, bool uniform, int fused);
 // Tile widths of the per-tile kernels; with `env_override` the widths asked

@@ -103,6 +103,13 @@ int zpitch(int M) { return M + (M >> 4) + 1; }
 size_t z_smem(const Group &g, int dtype) { return (size_t)(g.M + (size_t)g.Wz * zpitch(g.M)) * csize(dtype); }
 size_t s_smem(int L, int W, int dtype) { return (size_t)L * (1 + W) * csize(dtype); }
 
+bool tiles_fit(const Group &g, int dtype)
+{
+    const bool fp64 = dtype == PSOLVE_F64;
+    return g.Wz * g.pz.TL <= max_threads(fp64, g.pz.E) && g.Wy * g.py.TL <= max_threads(fp64, g.py.E) &&
+           g.Wx * g.px.TL <= max_threads(fp64, g.px.E);
+}
+
 bool fused_ok(const Group &g, int dtype, bool uniform, int fused)
 {
     if (!uniform || dtype != PSOLVE_F32) return false;
@@ -434,6 +441,10 @@ psolve_status build_plan(const std::vector<int> &nx, const std::vector<int> &ny,
             !make_line_plan(g.nx, g.px, 0, e3cap))
             return fail(PSOLVE_ERR_UNSUPPORTED_SIZE, "no stage plan for this size");
         choose_tiles(g, dtype);
+        if (!tiles_fit(g, dtype))
+            return fail(PSOLVE_ERR_UNSUPPORTED_SIZE,
+                        "no tile of this grid fits a block (FP64 x lines of 1458 = 2·3^6 points: 486 threads for "
+                        "the two columns the x pass needs, 256 allowed)");
         for (int L : {g.M, g.ny, g.nx})
             if (!roots_at.count(L)) { roots_at[L] = tcount; tcount += L; }
         if (!post_at.count(g.nz)) { post_at[g.nz] = tcount; tcount += g.M; }

@@ -50,6 +50,17 @@ def test_unsupported_sizes_rejected_before_any_cuda_call(lib, dims):
     assert b"2^a 3^b" in lib.psolve_last_error()
 
 
+def test_fp64_x_lines_of_1458_points_rejected(lib):
+    # the x pass's tile of two 1458-point FP64 lines needs 486 threads; the
+    # plan says so before any CUDA call (FP32 takes the same grid)
+    h = ctypes.c_void_p()
+    assert lib.psolve_plan_create(1458, 8, 8, _lib.F64, 1, ctypes.byref(h)) == 2
+    assert b"1458" in lib.psolve_last_error()
+    ok = (ctypes.c_int * 2)(1458, 8)
+    eight = (ctypes.c_int * 2)(8, 8)
+    assert lib.psolve_plan_create_many(ok, eight, eight, 2, _lib.F64, ctypes.byref(h)) == 2
+
+
 def test_bad_arguments_rejected(lib):
     h = ctypes.c_void_p()
     assert lib.psolve_plan_create(8, 8, 8, _lib.F32, 0, ctypes.byref(h)) == 1

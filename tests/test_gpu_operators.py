@@ -47,6 +47,13 @@ def test_operator_parity(shape, prec, op, c):
     _check(shape, prec, op, c)
 
 
+@pytest.mark.parametrize("shape", [(16, 54, 2048), (1536, 16, 54), (8, 12, 1728)])
+def test_fd_operator_fp64_fine_lines(shape):
+    # lowest modes of 1728-2048-point lines: the stencil eigenvalues there
+    # are small differences, evaluated without cancellation on both sides
+    _check(shape, "f64", "fd", 0.0)
+
+
 @pytest.mark.parametrize("op,c", OPS[:2])
 def test_operator_tensor_cores(op, c):
     _check((512, 512, 32), "f32_tc", op, c)

@@ -51,6 +51,16 @@ def test_random_field_parity(prec, shape):
     check(u, oracle.solve(f_in.astype(np.float64)), prec, shape)
 
 
+@pytest.mark.parametrize("prec,shape", [("f32", (1458, 12, 16)), ("f32", (16, 1458, 8)), ("f64", (16, 1458, 8)),
+                                        ("f64", (8, 12, 1458))])
+def test_lines_of_1458_points(prec, shape):
+    # 2·3^6: six radix-3 stages; 243 threads per line (FP64 x lines of this
+    # length are refused at plan creation, the other axes are not)
+    f64 = wl.random_field(shape, seed=1458 + sum(shape))
+    u, f_in = gpu_solve(f64, prec)
+    check(u, oracle.solve(f_in.astype(np.float64)), prec, shape)
+
+
 # Lines of 256/512/1024 points go through the persistent TMA-fed y/x passes
 # in FP32 (column tiles of 32/16/8); 96 and 48 leave a ragged last tile.
 TMA_SHAPES = [(256, 512, 96), (512, 256, 32), (1024, 256, 16), (256, 1024, 48), (512, 512, 64),
