@@ -217,13 +217,19 @@ __global__ void __launch_bounds__(TmaShape<L, CFG>::NT, TmaShape<L, CFG>::MINB)
             if constexpr (!OPS) {
                 // the Poisson multiplier (the instantiation for other
                 // operators is separate, so this one keeps its registers)
-                const int kyz = ky * ky + col * col;
+                // Point x = t + m·TL has kx = t + c with c = m·TL for m < E/2
+                // and c = (m - E)·TL beyond (at m = E/2, t = 0 that is -L/2,
+                // whose square is the Nyquist mode's (+L/2)²), so |k|² =
+                // (t² + ky² + kz²) + c·2t + c² with c compile-time: two FP32
+                // operations per point, exact (integers below 2^24), and only
+                // m = 0 can hold k = 0.
+                const float base = (float)(t * t + ky * ky + col * col), t2 = (float)(2 * t);
 #pragma unroll
                 for (int m = 0; m < E; ++m) {
-                    const int kx = kvec_dev(t + m * TL, L);
-                    const int k2 = kx * kx + kyz;
+                    const int c = (2 * m < E ? m : m - E) * TL;
+                    const float k2 = fmaf((float)c, t2, base + (float)(c * c));
                     // coef·(1/k²) with the hardware reciprocal: about 2 ulp in FP32
-                    const float d = (k2 == 0) ? 0.f : __fdividef(a.coef, (float)k2);
+                    const float d = (m == 0 && k2 == 0.f) ? 0.f : __fdividef(a.coef, k2);
                     v[m] = cscale(v[m], d);
                 }
             } else if (a.op.op == 1) {
