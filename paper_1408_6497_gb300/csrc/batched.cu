@@ -20,8 +20,15 @@
 #include "launch.h"
 #include "tma.cuh"
 
+// Resident blocks per SM the kernel is compiled for: eight, at 64 registers a
+// thread.  The tiles are latency-bound, so warps in flight count for more
+// than the spills a lower register budget brings (64-grid batch on GB300:
+// 1.26 ms with four blocks per SM at 128 registers, 1.12 with five, 1.03 with
+// six, 1.02 with seven, 1.006 with eight; with 8 points per thread on the
+// 2^a-point lines instead of 16: 1.017 ms at eight blocks, 1.034 at ten,
+// 1.18 at twelve).
 #ifndef PSOLVE_BATCH_MINB
-#define PSOLVE_BATCH_MINB 4
+#define PSOLVE_BATCH_MINB 8
 #endif
 
 namespace psolve {
@@ -47,56 +54,128 @@ __device__ bool wait_count(const int *counter, long long need, unsigned long lon
     }
 }
 
+// Block-private scheduling state, in shared memory, written by thread 0 only.
+struct Sched {
+    long long item, next;  // the item being run; the one claimed after it
+    int seg, next_seg;     // their segments
+    int next_ready;        // the next item's dependency is known to be met
+    int okseg;             // a segment whose dependency this block has seen met
+    int pend;              // segment of a finished item not yet published, or -1
+    int claimed;           // the next item of the running one has been claimed
+    int abort;
+};
+
+// Publish the block's finished item: the barrier before this call orders
+// every thread's stores of that item before thread 0's fence (cumulative at
+// GPU scope), then one count.
+__device__ __forceinline__ void publish(Sched &s, int *done)
+{
+    if (s.pend >= 0) {
+        __threadfence();
+        atomicAdd(&done[s.pend], 1);
+        s.pend = -1;
+    }
+}
+
+// Claim the item after the running one and look (without waiting) whether
+// its dependency is met.
+template <typename T>
+__device__ __forceinline__ void claim_next(Sched &s, const BatchSeg<T> *segs, int nseg, long long total,
+                                           unsigned long long *work, int *done)
+{
+    const long long nx = (long long)atomicAdd(work, 1ull);
+    int sg = s.seg;
+    while (sg + 1 < nseg && segs[sg + 1].first <= nx) ++sg;
+    s.next = nx;
+    s.next_seg = sg;
+    int ready = 1;
+    if (nx < total && sg != s.okseg) {
+        const int dep = segs[sg].dep;
+        ready = dep < 0 || ld_acquire(&done[dep]) >= segs[sg].need;
+        if (ready) s.okseg = sg;
+    }
+    s.next_ready = ready;
+    s.claimed = 1;
+}
+
+// Called by every thread of the block once the tile's loads are issued:
+// thread 0 publishes the previous item and claims the next while the loads
+// are in flight.
+template <typename T> struct SchedHook {
+    Sched *s;
+    const BatchSeg<T> *segs;
+    int nseg;
+    long long total;
+    unsigned long long *work;
+    int *done;
+    __device__ __forceinline__ void operator()() const
+    {
+        if (threadIdx.x == 0) {
+            publish(*s, done);
+            claim_next<T>(*s, segs, nseg, total, work, done);
+        }
+    }
+};
+
 // One tile of one pass; LC > 0: the line length, with its compile-time plan.
 // Not inlined: each variant gets its own register allocation (a tile is
 // thousands of instructions, so the call costs nothing measurable).
 template <typename T, int E, int LC> __device__ __noinline__ void run_item(const BatchSeg<T> *__restrict__ sgp,
                                                                           long long tile, const T *f, T *u,
-                                                                          unsigned char *smem)
+                                                                          unsigned char *smem,
+                                                                          const SchedHook<T> *hk)
 {
     const BatchSeg<T> &sg = *sgp;
     T *ui = u + sg.off;
+    const SchedHook<T> &h = *hk;
     switch (sg.kind) {
-    case 0: zfwd_tile<T, E, LC, true>(sg.z, f + sg.off, ui, tile, smem); break;
-    case 1: ypass_tile<T, E, false, LC, true>(sg.y, ui, tile, smem); break;
-    case 2: xfused_tile<T, E, LC, true>(sg.x, ui, tile, smem); break;
-    case 3: ypass_tile<T, E, true, LC, true>(sg.y, ui, tile, smem); break;
-    default: zinv_tile<T, E, LC, true>(sg.z, ui, ui, tile, smem); break;
+    case 0: zfwd_tile<T, E, LC, true>(sg.z, f + sg.off, ui, tile, smem, h); break;
+    case 1: ypass_tile<T, E, false, LC, true>(sg.y, ui, tile, smem, h); break;
+    case 2: xfused_tile<T, E, LC, true>(sg.x, ui, tile, smem, h); break;
+    case 3: ypass_tile<T, E, true, LC, true>(sg.y, ui, tile, smem, h); break;
+    default: zinv_tile<T, E, LC, true>(sg.z, ui, ui, tile, smem, h); break;
     }
 }
 
 // Compile-time plans: 2^a-point lines with 16 points per thread, 3·2^a-point
 // lines with 12 (the run-time planner's choices for batches).
 template <typename T> __device__ __forceinline__ void run_item_any(const BatchSeg<T> &sg, long long tile,
-                                                                   const T *f, T *u, unsigned char *smem)
+                                                                   const T *f, T *u, unsigned char *smem,
+                                                                   const SchedHook<T> *h)
 {
     switch (sg.E) {
-    case 4: run_item<T, 4, 0>(&sg, tile, f, u, smem); break;
-    case 8: run_item<T, 8, 0>(&sg, tile, f, u, smem); break;
+    case 4: run_item<T, 4, 0>(&sg, tile, f, u, smem, h); break;
+    case 8: run_item<T, 8, 0>(&sg, tile, f, u, smem, h); break;
     case 12:
         switch (sg.lc) {
-        case 12: run_item<T, 12, 12>(&sg, tile, f, u, smem); break;
-        case 24: run_item<T, 12, 24>(&sg, tile, f, u, smem); break;
-        case 48: run_item<T, 12, 48>(&sg, tile, f, u, smem); break;
-        case 96: run_item<T, 12, 96>(&sg, tile, f, u, smem); break;
-        case 192: run_item<T, 12, 192>(&sg, tile, f, u, smem); break;
-        default: run_item<T, 12, 0>(&sg, tile, f, u, smem); break;
+        case 12: run_item<T, 12, 12>(&sg, tile, f, u, smem, h); break;
+        case 24: run_item<T, 12, 24>(&sg, tile, f, u, smem, h); break;
+        case 48: run_item<T, 12, 48>(&sg, tile, f, u, smem, h); break;
+        case 96: run_item<T, 12, 96>(&sg, tile, f, u, smem, h); break;
+        case 192: run_item<T, 12, 192>(&sg, tile, f, u, smem, h); break;
+        default: run_item<T, 12, 0>(&sg, tile, f, u, smem, h); break;
         }
         break;
     case 16:
         switch (sg.lc) {
-        case 16: run_item<T, 16, 16>(&sg, tile, f, u, smem); break;
-        case 32: run_item<T, 16, 32>(&sg, tile, f, u, smem); break;
-        case 64: run_item<T, 16, 64>(&sg, tile, f, u, smem); break;
-        case 128: run_item<T, 16, 128>(&sg, tile, f, u, smem); break;
-        case 256: run_item<T, 16, 256>(&sg, tile, f, u, smem); break;
-        default: run_item<T, 16, 0>(&sg, tile, f, u, smem); break;
+        case 16: run_item<T, 16, 16>(&sg, tile, f, u, smem, h); break;
+        case 32: run_item<T, 16, 32>(&sg, tile, f, u, smem, h); break;
+        case 64: run_item<T, 16, 64>(&sg, tile, f, u, smem, h); break;
+        case 128: run_item<T, 16, 128>(&sg, tile, f, u, smem, h); break;
+        case 256: run_item<T, 16, 256>(&sg, tile, f, u, smem, h); break;
+        default: run_item<T, 16, 0>(&sg, tile, f, u, smem, h); break;
         }
         break;
     default: break;
     }
 }
 
+// Items are taken in order; thread 0 claims the next one and checks its
+// dependency while the running item's loads are in flight, and publishes a
+// finished item one item later (or before it waits, or at exit), so that no
+// fence, atomic or dependency load sits between two items.  A block never
+// waits with an unpublished item, so the argument above still holds: the
+// lowest unfinished item depends only on published ones.
 template <typename T>
 __global__ void __launch_bounds__(kBatchThreads, PSOLVE_BATCH_MINB) k_batched(const BatchSeg<T> *segs, int nseg,
                                                               long long total, const T *f, T *u,
@@ -104,44 +183,47 @@ __global__ void __launch_bounds__(kBatchThreads, PSOLVE_BATCH_MINB) k_batched(co
                                                               unsigned long long wait_ns)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
-    __shared__ long long s_item, s_next;
-    __shared__ int s_seg, s_abort;
+    __shared__ Sched s;
+    const SchedHook<T> hook{&s, segs, nseg, total, work, done};
     if (threadIdx.x == 0) {
-        s_next = (long long)atomicAdd(work, 1ull);
-        s_seg = 0;
+        s.seg = 0;
+        s.okseg = -1;
+        s.pend = -1;
+        claim_next<T>(s, segs, nseg, total, work, done);
     }
     while (true) {
-        __syncthreads(); // the previous item's shared-memory reads are finished
         if (threadIdx.x == 0) {
-            s_item = s_next;
-            s_abort = 0;
-            if (s_item < total) {
-                // Items grow per block: walk forward from the last segment.
-                int sgi = s_seg;
-                while (sgi + 1 < nseg && segs[sgi + 1].first <= s_item) ++sgi;
-                s_seg = sgi;
-                const int dep = segs[sgi].dep;
-                if (dep >= 0 && !wait_count(&done[dep], segs[sgi].need, wait_ns)) {
-                    s_abort = 1;
+            // (the previous item's stores and shared-memory reads are ordered
+            // by the barrier that ended it: run_item_any's callers reach here
+            // only after the barrier below)
+            if (!s.claimed) claim_next<T>(s, segs, nseg, total, work, done);
+            s.item = s.next;
+            s.seg = s.next_seg;
+            s.claimed = 0;
+            s.abort = 0;
+            if (s.item < total && !s.next_ready) {
+                publish(s, done);
+                const BatchSeg<T> &sg = segs[s.seg];
+                if (wait_count(&done[sg.dep], sg.need, wait_ns)) {
+                    s.okseg = s.seg;
+                } else {
+                    s.abort = 1;
                     atomicExch(status, (int)PSOLVE_ERR_TIMEOUT);
                 }
-                // Take the next item now; it is only claimed, not started.
-                s_next = (long long)atomicAdd(work, 1ull);
             }
         }
         __syncthreads();
-        const long long item = s_item;
-        if (item >= total || s_abort) return;
-        const BatchSeg<T> &sg = segs[s_seg];
-        const long long tile = item - sg.first;
-        run_item_any<T>(sg, tile, f, u, smraw);
-        // Publish this tile: the barrier orders every thread's stores before
-        // thread 0's fence (cumulative at GPU scope), then one count.
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            __threadfence();
-            atomicAdd(&done[s_seg], 1);
+        const long long item = s.item;
+        if (item >= total || s.abort) {
+            if (threadIdx.x == 0 && !s.abort) publish(s, done);
+            return;
         }
+        const BatchSeg<T> &sg = segs[s.seg];
+        run_item_any<T>(sg, item - sg.first, f, u, smraw, &hook);
+        // Every thread's stores of this item and its shared-memory reads are
+        // finished before thread 0 claims, publishes or the next item starts.
+        __syncthreads();
+        if (threadIdx.x == 0) s.pend = s.seg;
     }
 }
 

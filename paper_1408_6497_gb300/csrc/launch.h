@@ -123,9 +123,9 @@ cudaError_t launch_zy_cluster(const CUtensorMap &map, const ZyArgs &a, int M, in
                               cudaStream_t s, bool pdl = true);
 
 // Persistent batched kernel: one segment per (pass, instance), pass-major.
-// Threads of a batched-launch block: 128, four blocks per SM (measured on
-// GB300 for the 64-grid batch: 1.36 ms against 1.51 ms with 256-thread blocks
-// two per SM; the barriers of a tile then hold four warps, not eight).
+// Threads of a batched-launch block: 128 (the barriers of a tile hold four
+// warps; 256-thread blocks measured slower on GB300), eight blocks per SM
+// (PSOLVE_BATCH_MINB in batched.cu).
 #ifndef PSOLVE_BATCH_THREADS
 #define PSOLVE_BATCH_THREADS 128
 #endif

@@ -114,12 +114,18 @@ template <bool CG, typename C> __device__ __forceinline__ C ld_data(const C *p)
 // Every tile function below is called by all threads of a block (it
 // synchronises); threads beyond the tile's W·TL lanes are idle.  `smem` is
 // the block's dynamic shared memory: the line's twiddle table, then the
-// exchange buffer.
+// exchange buffer.  `hook` is called once by every thread as soon as the
+// tile's global loads are issued, before the first barrier: the persistent
+// batched kernel schedules its next item there, while the loads are in
+// flight; the one-pass kernels pass the no-op.
+struct NoHook {
+    __device__ __forceinline__ void operator()() const {}
+};
 
 // --------------------------------------------------------------- z forward
-template <typename T, int E, int LC, bool CG = false>
+template <typename T, int E, int LC, bool CG = false, class Hook = NoHook>
 __device__ __forceinline__ void zfwd_tile(const ZArgs<T> &a, const T *in, T *out, long long tile,
-                                          unsigned char *smem)
+                                          unsigned char *smem, const Hook &hook = Hook())
 {
     using C = typename cplx_of<T>::type;
     C *stw = reinterpret_cast<C *>(smem);
@@ -140,6 +146,7 @@ __device__ __forceinline__ void zfwd_tile(const ZArgs<T> &a, const T *in, T *out
 #pragma unroll
         for (int m = 0; m < E; ++m) v[m] = C{0, 0};
     }
+    hook();
     __syncthreads();
     const int LP = M + (M >> 4) + 1;
     const MapRow<> map{w * LP};
@@ -170,9 +177,9 @@ __device__ __forceinline__ void zfwd_tile(const ZArgs<T> &a, const T *in, T *out
 }
 
 // --------------------------------------------------------------- z inverse
-template <typename T, int E, int LC, bool CG = false>
+template <typename T, int E, int LC, bool CG = false, class Hook = NoHook>
 __device__ __forceinline__ void zinv_tile(const ZArgs<T> &a, const T *in, T *out, long long tile,
-                                          unsigned char *smem)
+                                          unsigned char *smem, const Hook &hook = Hook())
 {
     using C = typename cplx_of<T>::type;
     C *stw = reinterpret_cast<C *>(smem);
@@ -191,6 +198,9 @@ __device__ __forceinline__ void zinv_tile(const ZArgs<T> &a, const T *in, T *out
         const C *src = reinterpret_cast<const C *>(in) + row * M + t;
 #pragma unroll
         for (int m = 0; m < E; ++m) v[m] = ld_data<CG>(src + m * TL);
+    }
+    hook();
+    if (active) {
 #pragma unroll
         for (int m = 0; m < E; ++m) sx[map(t + m * TL)] = v[m];
     }
@@ -223,8 +233,9 @@ __device__ __forceinline__ void zinv_tile(const ZArgs<T> &a, const T *in, T *out
 }
 
 // ------------------------------------------------------- strided c2c (y)
-template <typename T, int E, bool INV, int LC, bool CG = false>
-__device__ __forceinline__ void ypass_tile(const SArgs<T> &a, T *data, long long tile, unsigned char *smem)
+template <typename T, int E, bool INV, int LC, bool CG = false, class Hook = NoHook>
+__device__ __forceinline__ void ypass_tile(const SArgs<T> &a, T *data, long long tile, unsigned char *smem,
+                                           const Hook &hook = Hook())
 {
     using C = typename cplx_of<T>::type;
     C *stw = reinterpret_cast<C *>(smem);
@@ -248,6 +259,7 @@ __device__ __forceinline__ void ypass_tile(const SArgs<T> &a, T *data, long long
 #pragma unroll
         for (int m = 0; m < E; ++m) v[m] = C{0, 0};
     }
+    hook();
     __syncthreads();
     const MapStrided map{W, w};
     line_fft_any<INV, LC>(v, t, a.pl, stw, sx, map, active);
@@ -267,12 +279,12 @@ __device__ __forceinline__ void ypass_tile(const SArgs<T> &a, T *data, long long
 // block must call it (it synchronises).
 // G: x-split factor of the spectrum layout (1: natural; else TL % G == 0).
 // OPS = false: the Poisson multiplier only (op is not read).
-template <typename T, int E, int LC, bool CG = false, bool OPS = true>
+template <typename T, int E, int LC, bool CG = false, bool OPS = true, class Hook = NoHook>
 __device__ __forceinline__ void xpair_block(T *data, int nx_rt, int ny, int M, long long sInst, long long npairs,
                                             T coef, const OpArgs &op, const LinePlan &pl, int W, int TL,
                                             long long pidx, int t,
                                             int w, const typename cplx_of<T>::type *stw,
-                                            typename cplx_of<T>::type *sx, int G = 1)
+                                            typename cplx_of<T>::type *sx, int G = 1, const Hook &hook = Hook())
 {
     using C = typename cplx_of<T>::type;
     const int nx = LC > 0 ? LC : nx_rt;
@@ -298,6 +310,7 @@ __device__ __forceinline__ void xpair_block(T *data, int nx_rt, int ny, int M, l
 #pragma unroll
         for (int m = 0; m < E; ++m) v[m] = C{0, 0};
     }
+    hook();
     __syncthreads();
     line_fft_any<false, LC>(v, t, pl, stw, sx, map, active);
     if (active) {
@@ -341,8 +354,9 @@ __device__ __forceinline__ void xpair_block(T *data, int nx_rt, int ny, int M, l
 // ----------------------------------- x forward, spectral division, x inverse
 // Tiles [0, main_tiles) are (instance, y, column block); the following ones
 // are groups of packed-column pairs.
-template <typename T, int E, int LC, bool CG = false>
-__device__ __forceinline__ void xfused_tile(const XArgs<T> &a, T *data, long long tile, unsigned char *smem)
+template <typename T, int E, int LC, bool CG = false, class Hook = NoHook>
+__device__ __forceinline__ void xfused_tile(const XArgs<T> &a, T *data, long long tile, unsigned char *smem,
+                                            const Hook &hook = Hook())
 {
     using C = typename cplx_of<T>::type;
     C *stw = reinterpret_cast<C *>(smem);
@@ -357,8 +371,8 @@ __device__ __forceinline__ void xfused_tile(const XArgs<T> &a, T *data, long lon
     const MapStrided map{W, w};
 
     if (tile >= a.main_tiles) {
-        xpair_block<T, E, LC, CG>(data, nx, ny, M, a.sInst, a.npairs, a.coef, a.op, a.pl, W, TL, tile - a.main_tiles,
-                                  t, w, stw, sx);
+        xpair_block<T, E, LC, CG, true, Hook>(data, nx, ny, M, a.sInst, a.npairs, a.coef, a.op, a.pl, W, TL,
+                                              tile - a.main_tiles, t, w, stw, sx, 1, hook);
         return;
     }
     C v[E];
@@ -376,6 +390,7 @@ __device__ __forceinline__ void xfused_tile(const XArgs<T> &a, T *data, long lon
 #pragma unroll
         for (int m = 0; m < E; ++m) v[m] = C{0, 0};
     }
+    hook();
     __syncthreads();
     line_fft_any<false, LC>(v, t, a.pl, stw, sx, map, active);
     const int ky = kvec_dev(y, ny);
