@@ -253,8 +253,11 @@ template <typename T> psolve_status setup_batched(psolve_plan *p)
     std::vector<BatchSeg<T>> segs(5 * (size_t)B);
     long long first = 0;
     size_t smem = 0;
-    // Line plans in the radix order the knobs select (the tables are per length).
-    for (auto &g : p->groups) {
+    // Line plans in the radix order the knobs select (the tables are per
+    // length), on a copy: the plan's groups change only once the whole
+    // schedule is known to fit.
+    std::vector<Group> gs = p->groups;
+    for (auto &g : gs) {
         make_line_plan(g.M, g.pz, p->bknob[3], 2);
         make_line_plan(g.ny, g.py, p->bknob[4], 2);
         make_line_plan(g.nx, g.px, p->bknob[5], 2);
@@ -268,7 +271,7 @@ template <typename T> psolve_status setup_batched(psolve_plan *p)
     };
     for (int pass = 0; pass < 5; ++pass) {
         for (int i = 0; i < B; ++i) {
-            const Group &g = p->groups[i];
+            const Group &g = gs[i];
             BatchSeg<T> sg;
             std::memset(&sg, 0, sizeof(sg));
             sg.kind = pass;
@@ -308,6 +311,7 @@ template <typename T> psolve_status setup_batched(psolve_plan *p)
             } else {
                 int W = std::max(2, std::min(std::max(2, M), NT / g.px.TL / p->bknob[2]));
                 while (W > 2 && s_smem(g.nx, W, p->dtype) > kSmemCap) W /= 2;
+                // (the caller then launches per pass and instance)
                 if (W * g.px.TL > NT) return fail(PSOLVE_ERR_UNSUPPORTED_SIZE, "x line too long for a batch tile");
                 sg.E = g.px.E;
                 sg.lc = lc_of(g.px, p->bknob[5]);
@@ -334,6 +338,7 @@ template <typename T> psolve_status setup_batched(psolve_plan *p)
     }
     for (auto &sg : segs)
         if (sg.dep >= 0) sg.need = (int)segs[sg.dep].ntiles;
+    p->groups = gs;
     p->nseg = (int)segs.size();
     p->total_items = first;
     p->batch_smem = smem;
@@ -572,8 +577,12 @@ psolve_status build_plan(const std::vector<int> &nx, const std::vector<int> &ny,
             for (const auto &g : p->groups)
                 ok = ok && batched_supports_E(g.pz.E) && batched_supports_E(g.py.E) && batched_supports_E(g.px.E);
             if (ok) {
+                // a grid whose x lines do not fit a batch tile keeps the
+                // launches per pass and instance
                 psolve_status st = setup_batched<float>(p.get());
-                if (st != PSOLVE_OK) {
+                if (st == PSOLVE_ERR_UNSUPPORTED_SIZE) {
+                    drop_batched(p.get());
+                } else if (st != PSOLVE_OK) {
                     release(p.release());
                     return st;
                 }

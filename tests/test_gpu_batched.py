@@ -110,6 +110,19 @@ def test_batched_matches_per_instance_launches(monkeypatch):
         assert float((a - r).norm() / r.norm()) <= 1e-6
 
 
+def test_x_lines_too_long_for_a_batch_tile_run_per_pass():
+    # 2048-point x lines need two 128-thread columns (256 threads) in the x
+    # pass: the plan keeps one launch per pass and instance instead of failing
+    shapes = [(2048, 4, 8), (8, 8, 8), (24, 48, 32)]
+    plan = Plan(dtype="f32", shapes=shapes)
+    assert plan.launches_per_solve == 5 * len(shapes)
+    flat, fs = fill(plan, shapes, seed_offset=70)
+    u = plan.execute(flat)
+    plan.status()
+    for b, s in enumerate(shapes):
+        check(plan.view(u, b).cpu().numpy(), oracle.solve(fs[b].astype(np.float64)), "f32", s)
+
+
 def test_bounded_wait_reports_timeout_and_context_survives():
     lib = _lib.load()
     shapes = [(8, 8, 8), (16, 8, 8)]
