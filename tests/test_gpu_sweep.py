@@ -1,6 +1,9 @@
 """Randomized parity sweep: seeded draws of grid shape (every axis a valid
 2^a·3^b size from 4 to 2048), precision, operator and batch, each solved
-through the C ABI and compared with the FP64 oracle at the parity bounds.
+through the C ABI and compared with the FP64 oracle at the parity bounds;
+and seeded draws of uneven batches (2 to 6 unequal grids in one plan, most
+of them on axis lengths the persistent batched kernel plans, so that its
+schedule meets tiles of many lengths in one launch).
 
 The fixed cases elsewhere pick the configurations each kernel was written
 for; this sweep reaches the combinations nobody picked (odd M = nz/2,
@@ -26,6 +29,7 @@ pytestmark = pytest.mark.gpu
 
 SIZES = sorted({2 ** a * 3 ** b for a in range(1, 12) for b in range(7) if 4 <= 2 ** a * 3 ** b <= 2048})
 CASES = 160
+BATCH_CASES = 48
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -67,3 +71,50 @@ def test_random_case(i):
     u = u.cpu().numpy().reshape((batch,) + shape)
     for b in range(batch):
         check(u[b], oracle.solve(f[b].astype(np.float64), op=op, c=c), prec, (shape, prec, op, batch, b))
+
+
+# axis lengths whose lines the persistent batched kernel plans (12 or 16
+# points per thread, at most 64 threads a line)
+BATCH_SIZES = [16, 24, 32, 48, 64, 96, 128, 192, 256, 384, 512, 768, 1024]
+
+
+def draw_uneven(i):
+    rng = random.Random(20142000 + i)
+    prec = rng.choice(["f32", "f32", "f32", "f64"])
+    limit = 2 ** 22 if prec == "f64" else 2 ** 23
+    sizes = BATCH_SIZES if rng.random() < 0.75 else SIZES
+    count = rng.randint(2, 6)
+    shapes = []
+    for _ in range(1000):
+        if len(shapes) == count:
+            break
+        shape = tuple(rng.choice(sizes) for _ in range(3))
+        n = int(np.prod(shape))
+        if n <= limit // count and not (prec == "f64" and shape[0] == 1458):
+            shapes.append(shape)
+    assert len(shapes) == count
+    op, c = rng.choice([("poisson", 0.0), ("poisson", 0.0), ("helmholtz", 3.0), ("fd", 0.0)])
+    return shapes, prec, op, c, sizes is BATCH_SIZES
+
+
+@pytest.mark.parametrize("i", range(BATCH_CASES))
+def test_random_uneven_batch(i):
+    # unequal grids in one plan: the persistent batched launch where every
+    # line fits its tiles (always for FP32 grids of BATCH_SIZES axes), else
+    # one launch per pass and instance
+    shapes, prec, op, c, batchable = draw_uneven(i)
+    npt = np.float64 if prec == "f64" else np.float32
+    plan = Plan(dtype=prec, shapes=shapes, operator=op, c=c)
+    if batchable and prec == "f32":
+        assert plan.launches_per_solve == 1, shapes
+    flat = plan.empty()
+    fs = []
+    for b, s in enumerate(shapes):
+        f = wl.random_field(s, seed=977 * i + b).astype(npt)
+        fs.append(f)
+        plan.view(flat, b).copy_(torch.from_numpy(f))
+    u = plan.execute(flat)
+    plan.status()
+    for b, s in enumerate(shapes):
+        check(plan.view(u, b).cpu().numpy(), oracle.solve(fs[b].astype(np.float64), op=op, c=c), prec,
+              (s, prec, op, b, plan.launches_per_solve))
