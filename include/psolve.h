@@ -102,7 +102,14 @@ psolve_status psolve_plan_create(int nx, int ny, int nz, int dtype, int batch,
 
 /* Create a plan for `batch` grids of unequal sizes (nx[b], ny[b], nz[b]),
  * solved together.  Instance b starts at element psolve_instance_offset(b)
- * of the packed f/u arrays; offsets are aligned up to 32 elements. */
+ * of the packed f/u arrays; offsets are aligned up to 32 elements.  FP32
+ * plans whose every line fits a 128-thread tile (at most 16 points a
+ * thread, 12 for lengths 3·2^a; x lines of at most 64 threads) solve every
+ * pass of every instance in one persistent kernel launched from a CUDA
+ * graph; other plans (FP64, or lines such as 2048 points or 2·3^b points)
+ * launch each pass of each instance in turn, with the same results to
+ * rounding.  psolve_launches_per_solve tells which.  Size rules and errors
+ * as psolve_plan_create. */
 psolve_status psolve_plan_create_many(const int *nx, const int *ny, const int *nz, int batch,
                                       int dtype, psolve_plan **out);
 
