@@ -115,7 +115,12 @@ psolve_status psolve_plan_create_many(const int *nx, const int *ny, const int *n
 
 /* u = A f for every instance (§2.1).  f, u: device pointers holding
  * psolve_total_elements(plan) values.  u == f (in place) is allowed; any
- * other overlap is PSOLVE_ERR_INVALID_ARG.  f is not modified unless u == f. */
+ * other overlap is PSOLVE_ERR_INVALID_ARG.  f is not modified unless u == f.
+ * Enqueued on `stream` without synchronising.  Solves of one plan must not
+ * overlap on the device: the plan's spectrum buffer (x-split plans), the
+ * persistent batched launch's work counters and the status word are shared
+ * by its solves, so solves on several streams need one plan per stream or
+ * streams ordered by events. */
 psolve_status psolve_execute(psolve_plan *plan, const void *f, void *u, void *stream);
 
 /* grad_f = A^T g.  A is real symmetric (D is real and even in k), so this is
