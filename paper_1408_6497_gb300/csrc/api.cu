@@ -340,7 +340,7 @@ psolve_status psolve_debug_set_wait(psolve_plan *plan, unsigned long long wait_n
     if (!plan->batched) return fail(PSOLVE_ERR_INVALID_ARG, "plan has no persistent batched launch");
     DeviceGuard dg(plan->device);
     plan->wait_ns = wait_ns;
-    // Segment nseg/5 (pass 1 of instance 0) waits on segment 0.
+    // Segment nseg/5 (the first of pass 1) waits on one segment of pass 0.
     const size_t seg_bytes = plan->segs_host.size() / (size_t)plan->nseg;
     const int target = plan->nseg / 5;
     unsigned char entry[4096];

@@ -269,13 +269,15 @@ template <typename T> psolve_status setup_batched(psolve_plan *p)
     auto lc_of = [&](const LinePlan &pl, int order) {
         return (use_ct && order == 0 && batched_ct_supported(pl.L, pl.E)) ? pl.L : 0;
     };
+    // segments by (pass, instance) first; ordered below
+    std::vector<BatchSeg<T>> raw(5 * (size_t)B);
     for (int pass = 0; pass < 5; ++pass) {
         for (int i = 0; i < B; ++i) {
             const Group &g = gs[i];
             BatchSeg<T> sg;
             std::memset(&sg, 0, sizeof(sg));
             sg.kind = pass;
-            sg.dep = pass == 0 ? -1 : (pass - 1) * B + i;
+            sg.dep = -1;
             sg.off = (long long)g.off0;
             const int M = g.M;
             if (pass == 0 || pass == 4) {
@@ -331,13 +333,39 @@ template <typename T> psolve_status setup_batched(psolve_plan *p)
                 sg.ntiles = sg.x.main_tiles + (sg.x.npairs + W / 2 - 1) / (W / 2);
                 smem = std::max(smem, s_smem(g.nx, W, p->dtype));
             }
-            sg.first = first;
-            first += sg.ntiles;
-            segs[(size_t)pass * B + i] = sg;
+            raw[(size_t)pass * B + i] = sg;
         }
     }
-    for (auto &sg : segs)
-        if (sg.dep >= 0) sg.need = (int)segs[sg.dep].ntiles;
+    // Within a pass the instances are ordered by tile variant (points per
+    // thread, compile-time line length), so that the blocks, which take items
+    // in order, run one variant's code at a time; passes stay in order, so
+    // every segment's dependency (the same instance's previous pass) lies on
+    // earlier items.  PSOLVE_BATCH_SORT = 0 keeps the instance order.
+    const char *se = std::getenv("PSOLVE_BATCH_SORT");
+    const bool by_variant = !(se && se[0] == '0');
+    std::vector<int> pos(5 * (size_t)B);
+    std::vector<int> order(B);
+    for (int pass = 0; pass < 5; ++pass) {
+        for (int i = 0; i < B; ++i) order[i] = i;
+        if (by_variant)
+            std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+                const BatchSeg<T> &a = raw[(size_t)pass * B + x], &b = raw[(size_t)pass * B + y];
+                return a.E != b.E ? a.E < b.E : a.lc < b.lc;
+            });
+        for (int k = 0; k < B; ++k) {
+            const size_t idx = (size_t)pass * B + k;
+            segs[idx] = raw[(size_t)pass * B + order[k]];
+            segs[idx].first = first;
+            first += segs[idx].ntiles;
+            pos[(size_t)pass * B + order[k]] = (int)idx;
+        }
+    }
+    for (int pass = 1; pass < 5; ++pass)
+        for (int i = 0; i < B; ++i) {
+            BatchSeg<T> &sg = segs[pos[(size_t)pass * B + i]];
+            sg.dep = pos[(size_t)(pass - 1) * B + i];
+            sg.need = (int)segs[sg.dep].ntiles;
+        }
     p->groups = gs;
     p->nseg = (int)segs.size();
     p->total_items = first;
